@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s of the dynamic-OT inexact proximal ALM at KKT <= 1e-6.
+
+One step = one complete solve (Algorithm 2 from q = alpha = beta = 0 until
+eta_dot <= tol at a check) of a seeded synthetic 2D 256^2 x 64 Gaussian-mixture
+transport problem, with its inputs already resident in HBM.  The mixed-precision
+path is the product; the FP64 path is solved once on the same GPU for the
+"mixed vs FP64" comparison.  Multi-GPU: independent replicas (one process per
+GPU, no collective on the data path), value = all solves / max wall time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  --impl reference times the CPU oracle (the
+plain FP64 restatement under oracle/) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at KKT<=1e-6, mixed vs FP64 on same GPU; p50/p99 latency; %HBM peak"
+WORKLOAD = "mix256"
+WORKLOAD_DESC = ("2D DOT 256x256 cells x 64 time steps, seeded mixtures of 1-5 Gaussians "
+                 "(means U[0.15,0.85]^2, sigma U[0.03,0.12], Dirichlet weights), pdf < 1e-4 -> 0")
+# Iterations the FP64 recurrence (GPU FP64 path == oracle, lock-step tested) needs to reach
+# eta_dot <= 1e-6 on the seed-1002 instance of this workload; converts the oracle's
+# seconds per iteration into solves/s in the reference arm.  Measured by this script's
+# own arm ("fp64" -> "iterations" in its JSON line).
+ORACLE_ITERS_PER_SOLVE = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--maxit", type=int, default=40000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--fp64-maxit", type=int, default=40000)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- algorithmic bytes ("Kernels and their rooflines") --------
+
+def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
+    """Compulsory DRAM bytes of one launch of `name` (natural, unpadded counts)."""
+    P = N ** D
+    nc, n0 = (T + 1) * P, T * P
+    nf = (T + 1) * N ** (D - 1) * (N - 1)          # faces of one spatial axis
+    K = 4 * D + 2
+    if prec == "fp64":
+        w, ws, wf = 8, 8, 8                        # q/z, multipliers, phi
+    else:
+        w, ws, wf = 4, 8, 8                        # FP32 q/z, two-float multipliers and phi
+    nq = n0 + D * nf
+    table = {
+        "assemble_b": (w + ws) * nq + w * nc,
+        "cone_project": w * nq + ws * K * n0 + w * K * n0,
+        "update_q0_alpha0": wf * nc + 2 * w * n0 + 2 * ws * n0 + ws * n0 + w * n0 + ws * n0,
+        "update_qd_alphad": wf * nc + 4 * w * n0 + 4 * ws * n0 + ws * nf + w * nf + ws * nf,
+        "update_beta": w * nq + w * K * n0 + 2 * ws * K * n0,
+        "dct_axis": 2 * (8 if prec == "fp64" else 4) * nc,
+        "poisson_residual": 3 * 4 * nc,
+        "poisson_combine": (4 + 4 + 8) * nc,
+        "dct_scale": 2 * (8 if prec == "fp64" else 4) * nc,
+    }
+    return float(table.get(name, 0.0))
+
+
+def make_solver(spec, r0, r1, mask, prec, **kw):
+    from paper_2505_05424_gb300.solver import DotSolver
+    return DotSolver(spec.D, spec.T, spec.N, r0, r1, mask=mask, prec=prec, **kw)
+
+
+def run_ours(args):
+    import torch
+    from paper_2505_05424_gb300 import workloads as W
+    from paper_2505_05424_gb300 import _native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _native.build()
+    _native.load()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    spec = W.MIX256
+    def instance(step):
+        r0, r1, m = W.mixture_pair(spec, 1002 + step + 1000 * rank)
+        return r0, r1, m
+
+    stream = torch.cuda.current_stream(dev)
+    # warm-up solves
+    for w in range(args.warmup):
+        r0, r1, m = instance(w)
+        s = make_solver(spec, r0, r1, m, args.prec)
+        s.dot_solve(args.tol, args.maxit)
+        s.close()
+    # inputs resident in HBM before the timed region
+    solvers = []
+    for k in range(args.steps):
+        r0, r1, m = instance(k)
+        s = make_solver(spec, r0, r1, m, args.prec)
+        s.dot_profile(True)
+        solvers.append(s)
+    launches0 = sum(s.launch_count() for s in solvers)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    lat, iters, etas, objs = [], [], [], []
+    ev0.record(stream)
+    for s in solvers:
+        t0 = time.perf_counter()
+        rc = s.dot_solve(args.tol, args.maxit)
+        lat.append((time.perf_counter() - t0) * 1e3)
+        kk = s.dot_kkt()
+        iters.append(int(kk["iterations"]))
+        etas.append(kk["eta_dot"])
+        objs.append(-2.0 * kk["primal_obj"])
+        if rc != 0:
+            print(json.dumps({"warning": f"solve did not converge (rc={rc})", "eta": kk["eta_dot"]}),
+                  file=sys.stderr)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    gpu_launches = sum(s.launch_count() for s in solvers) - launches0
+    prof = {}
+    for s in solvers:
+        for k, (ms, n) in s.dot_profile_read().items():
+            a = prof.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += n
+    for s in solvers:
+        s.close()
+    value = world * args.steps / (elapsed_ms / 1e3)
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = load_peaks()
+    # dominant kernel by total time in the timed region
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dn) = dom[0], dom[1]
+    per_launch_ms = dms / max(dn, 1)
+    abytes = algorithmic_bytes(dname, spec.D, spec.T, spec.N, args.prec)
+    if dname in ("dct_axis", "dct_tcgen05"):
+        M = spec.N
+        flops = 2.0 * M * (spec.T + 1) * spec.N ** spec.D * (3 if dname == "dct_tcgen05" else 1)
+        tf32_peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None, "kernel": dname,
+                "peak_source": f"{peak_src} bf16 sustained x tf32/bf16 nominal ratio 1.1/2.25"}
+    else:
+        achieved = abytes / (per_launch_ms / 1e3) / 1e9
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None, "kernel": dname,
+                "per_launch_ms": round(per_launch_ms, 5), "algorithmic_bytes": abytes,
+                "peak_source": f"{peak_src} (of measured copy bandwidth)" if peak_src == "measured" else peak_src}
+
+    kernels = {k: {"ms_total": round(v[0], 3), "launches": v[1],
+                   "ms_per_launch": round(v[0] / max(v[1], 1), 5),
+                   "GBps": (round(algorithmic_bytes(k, spec.D, spec.T, spec.N, args.prec)
+                                  / (v[0] / max(v[1], 1) / 1e3) / 1e9, 1)
+                            if algorithmic_bytes(k, spec.D, spec.T, spec.N, args.prec) > 0 and v[1] else None)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0]) if v[1]}
+
+    # e2e through the public API with host buffers: create (H2D) -> solve -> get (D2H)
+    e2e_lat = []
+    h2d = d2h = 0
+    for k in range(args.e2e_steps):
+        r0, r1, m = instance(100 + k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = make_solver(spec, r0, r1, m, args.prec)
+        s.dot_solve(args.tol, args.maxit)
+        rho, mm, phi, obj, kk = s.dot_get()
+        torch.cuda.synchronize()
+        e2e_lat.append(time.perf_counter() - t0)
+        s.close()
+        h2d = r0.nbytes + r1.nbytes + (0 if m is None else m.size)
+        d2h = rho.nbytes + sum(a.nbytes for a in mm) + phi.nbytes + 8 * 12
+    e2e_value = world * len(e2e_lat) / sum(e2e_lat) if e2e_lat else None
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "D": spec.D, "T": spec.T, "N": spec.N,
+                   "tol": args.tol, "prec": args.prec, "check_every": 10, "tau": 1.9,
+                   "l2": "inputs larger than L2 (per-solve state > 129 MB)", "seeds": "1002+step",
+                   "parallelism": f"replicas{world}"},
+        "iterations": iters, "eta_dot": etas, "objective": objs,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "it_per_s": round(sum(iters) / (elapsed_ms / 1e3), 1),
+        "clocks": clk, "gpu_launches": int(gpu_launches),
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": roof, "kernels": kernels,
+    }
+
+    # FP64 path on the same GPU, same instance as step 0
+    fp64_iters = None
+    if not args.no_fp64 and args.prec == "mixed":
+        r0, r1, m = instance(0)
+        s = make_solver(spec, r0, r1, m, "fp64")
+        s.dot_solve(args.tol, 20)          # warm the kernels
+        s.close()
+        s = make_solver(spec, r0, r1, m, "fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = s.dot_solve(args.tol, args.fp64_maxit)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        kk = s.dot_kkt()
+        s.close()
+        fp64_iters = int(kk["iterations"])
+        out["fp64"] = {"solves_per_s": (1.0 / dt) if rc == 0 else None, "seconds": round(dt, 3),
+                       "iterations": fp64_iters, "eta_dot": kk["eta_dot"], "converged": rc == 0,
+                       "ms_per_iter": round(dt * 1e3 / max(fp64_iters, 1), 3),
+                       "objective": -2.0 * kk["primal_obj"]}
+        if rc == 0:
+            out["mixed_vs_fp64"] = round(value / (1.0 / dt), 3)
+
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(fp64_iters or (iters[0] if iters else None))
+    print(json.dumps(out))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def oracle_seconds_per_iteration(n_iter: int):
+    """Time n_iter oracle iterations (plain FP64 C, OpenMP) on the seed-1002 instance."""
+    import oracle as O
+    from paper_2505_05424_gb300 import workloads as W
+    O.build()
+    spec = W.MIX256
+    r0, r1, m = W.mixture_pair(spec, 1002)
+    g = O.Grid(spec.D, spec.T, [spec.N] * spec.D)
+    prob = O.Problem(g, r0, r1, m)
+    st = O.State.zeros(g)
+    t0 = time.perf_counter()
+    for _ in range(n_iter):
+        O.iterate(prob, st)
+    return (time.perf_counter() - t0) / n_iter
+
+
+def cpu_baseline(iters_per_solve):
+    cores = len(os.sched_getaffinity(0))
+    spi = oracle_seconds_per_iteration(2)
+    val = (1.0 / (spi * iters_per_solve)) if iters_per_solve else None
+    return {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"2 oracle iterations of {WORKLOAD} ({spi:.2f} s/iteration, OpenMP on {cores} threads); "
+                      f"solves/s = 1 / (s/iteration x {iters_per_solve} iterations to eta<=1e-6)"}
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    iters = ORACLE_ITERS_PER_SOLVE
+    for _ in range(args.warmup):
+        oracle_seconds_per_iteration(1)
+    per = [oracle_seconds_per_iteration(1) for _ in range(args.steps)]
+    spi = float(np.mean(per))
+    cores = len(os.sched_getaffinity(0))
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "iterations-per-solve of the workload not recorded"}))
+        return
+    val = 1.0 / (spi * iters)
+    out = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": spi * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "tol": args.tol},
+           "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": f"each step = 1 oracle iteration; solves/s = 1/(s/it x {iters})"},
+           "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * dot.h -- C ABI of the GB300 (sm_103a) dynamic optimal transport solver.
+ *
+ * The solver runs the inexact proximal ALM of arXiv 2505.05424 (Algorithm 1,
+ * explicit steps Algorithm 2, Sec. 4) on the linear SOCP reformulation (Sec. 3,
+ * eq. (opt-dualsocalm-ran)) of the staggered-grid discretisation (Sec. 2.2,
+ * eq. (opt-disdualori)) of the Benamou-Brenier problem with quadratic cost, or of
+ * its weighted variant with obstacles (Sec. 5.4, eq. (opt-weightdualori)).
+ * Stopping test and penalty rule: Sec. 5.3.
+ *
+ * Grid.  D spatial axes (2 or 3) on [0,1]^D with N_d cells each; the potential
+ * phi lives on the cell centres (h_d = 1/N_d) so each spatial axis has N_d - 1
+ * interior faces; time [0,1] has T intervals and T+1 nodes (h_0 = 1/T).
+ *
+ * Host array layouts (all C-order, float64, owned by the caller; the library
+ * copies what it needs and never keeps a caller pointer after a call returns):
+ *   rho0, rho1, mask : [N_1]...[N_D]                    (cell-centred samples)
+ *   phi              : [T+1][N_1]...[N_D]                (nodes G^c)
+ *   rho              : [T][N_1]...[N_D]                  (time faces G^s_0)
+ *   m                : D blocks, block d of shape [T+1][..][N_d - 1][..]  (G^s_d)
+ *   q, alpha         : the concatenation (G^s_0; G^s_1; ...; G^s_D)
+ *   beta             : [4D+2][T][N_1]...[N_D]            (one cone per time face)
+ *
+ * Status codes: 0 success; < 0 error (the context, if any, stays valid unless
+ * the code is DOT_ECUDA); > 0 soft status with valid results.
+ * dot_last_error() returns a human-readable message for the last failing call on
+ * that context (or on the calling thread when ctx is NULL).
+ *
+ * Threading: contexts are independent; calls on different contexts may run
+ * concurrently from different threads, calls on one context must not.
+ */
+#ifndef DOT_GB300_H
+#define DOT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOT_OK 0
+#define DOT_EINVAL (-1)     /* bad argument: shape, non-finite or negative density, mass */
+#define DOT_ENOMEM (-2)     /* workspace too small or device allocation failed */
+#define DOT_ECUDA (-3)      /* a CUDA call failed; the context must be destroyed */
+#define DOT_EDIVERGED (-4)  /* a stopping measure became non-finite */
+#define DOT_ETIMEOUT (-5)   /* dot_options.max_seconds elapsed; state is readable */
+#define DOT_ENOTCONV 1      /* maxit reached before the tolerance; state is readable */
+
+typedef struct {
+  int D;      /* spatial dimension: 2 or 3 */
+  int T;      /* time intervals, >= 1 */
+  int N[3];   /* cells per spatial axis, each >= 2; N[d] for d >= D is ignored */
+} dot_grid;
+
+typedef enum {
+  DOT_FP64 = 0,   /* every field and every operation in FP64 (the reference path) */
+  DOT_MIXED = 1   /* FP32 stencils/projection, 3xTF32 DCT GEMMs on the tensor cores,
+                     two-float (48-bit) multipliers and potential, FP64 reductions,
+                     one refinement step of the Poisson solve per iteration */
+} dot_precision;
+
+typedef struct {
+  dot_precision prec;
+  double tau;              /* dual step length in (0, 2); Algorithm 1; default 1.9 (Sec. 5.2) */
+  double sigma0;           /* initial penalty sigma > 0; default 1 */
+  double s_sigma;          /* penalty factor s_sigma > 1; default 1.25 (Sec. 5.3) */
+  double s_r;              /* ratio threshold s_r > 1; default 2 (Sec. 5.3) */
+  int check_every;         /* evaluate the stopping measures and update sigma every
+                              check_every iterations; 0 = never; default 10 */
+  double obstacle_weight;  /* omega on masked cells (Sec. 5.4); default 1e-6 */
+  double max_seconds;      /* wall-clock limit per dot_solve call; 0 = none */
+} dot_options;
+
+/* Index of each value in the kkt[] array filled by dot_get / dot_kkt. */
+enum {
+  DOT_KKT_ETA = 0,        /* eta_dot = max(eta_P, eta_D, eta_C) (Sec. 5.3) */
+  DOT_KKT_ETA_P = 1,
+  DOT_KKT_ETA_D = 2,
+  DOT_KKT_ETA_C = 3,
+  DOT_KKT_ETA_P_SOC = 4,
+  DOT_KKT_ETA_D_SOC = 5,
+  DOT_KKT_PRIMAL = 6,     /* <c, phi>, the objective of problem (8) */
+  DOT_KKT_DUAL = 7,       /* dual objective (11) at the current alpha */
+  DOT_KKT_GAP = 8,        /* |primal - dual| / (1 + |primal| + |dual|) */
+  DOT_KKT_ITERS = 9,      /* iterations run since dot_create / dot_set_state */
+  DOT_KKT_SIGMA = 10,     /* current penalty */
+  DOT_KKT_LEN = 11
+};
+
+typedef struct dot_ctx dot_ctx;
+
+/* Fill *opt with the defaults listed above (prec = DOT_MIXED). */
+void dot_default_options(dot_options *opt);
+
+/* Device bytes a context of this grid and precision needs (for admission by HBM
+ * footprint).  Returns 0 for an invalid grid. */
+size_t dot_workspace_bytes(const dot_grid *grid, dot_precision prec);
+
+/* Create a solve.  rho0/rho1: non-negative finite samples, each with positive
+ * total mass; they are normalised to mass 1 and enter the problem as the vector
+ * c of eq. (defc).  mask: NULL or one byte per cell, non-zero = obstacle
+ * (omega = obstacle_weight there, Sec. 5.4).  opt: NULL = defaults.
+ * workspace: device memory of at least dot_workspace_bytes() bytes, 256-byte
+ * aligned, owned by the caller and kept alive until dot_destroy; NULL = the
+ * library allocates (and frees) it itself.  stream: cudaStream_t to run on;
+ * NULL = the legacy default stream.  The initial point is q = alpha = beta = 0,
+ * sigma = sigma0 (0 lies in Q, Algorithm 1's input condition).
+ * Returns DOT_EINVAL for bad shapes/densities, DOT_ENOMEM, or DOT_ECUDA. */
+int dot_create(const dot_grid *grid, const double *rho0, const double *rho1,
+               const uint8_t *mask, const dot_options *opt, void *workspace,
+               size_t workspace_bytes, void *stream, dot_ctx **out);
+
+/* Run Algorithm 2 until eta_dot <= tol at a check (Sec. 5.3) or maxit more
+ * iterations.  tol <= 0 never stops early.  Returns DOT_OK when converged,
+ * DOT_ENOTCONV at maxit, DOT_ETIMEOUT, DOT_EDIVERGED or DOT_ECUDA.  Blocks the
+ * calling thread at every check (it reads the stopping measures). */
+int dot_solve(dot_ctx *ctx, double tol, long maxit);
+
+/* Results.  Any pointer may be NULL.  rho = alpha_0 / h_0 and m_d = alpha_d / h_0
+ * (Proposition 3.3: (Lambda_0, Lambda_bar) = (alpha_0, alpha_bar) solve (12));
+ * objective = -2 <c, phi> (the squared Wasserstein-2 distance of the discrete
+ * problem); kkt: DOT_KKT_LEN values measured at the current iterate. */
+int dot_get(dot_ctx *ctx, double *rho, double *m, double *phi, double *objective, double *kkt);
+
+/* Stopping measures of the current iterate (Sec. 5.3) into kkt[DOT_KKT_LEN]. */
+int dot_kkt(dot_ctx *ctx, double *kkt);
+
+/* Checkpoint / warm start: the iterate (q, alpha, beta), sigma and the iteration
+ * count.  Layouts as in the file header; any output pointer may be NULL.  After
+ * dot_set_state the next iteration starts from the given point (phi and z are
+ * recomputed by Algorithm 2's first lines). */
+int dot_get_state(dot_ctx *ctx, double *q, double *alpha, double *beta, double *sigma, long *iters);
+int dot_set_state(dot_ctx *ctx, const double *q, const double *alpha, const double *beta,
+                  double sigma, long iters);
+
+/* Operator entry point: phi = (A^*A)^dagger b on rge(A^*) with the context's
+ * Poisson solver (DCT-II along every axis as dense GEMMs, scale by the inverse
+ * Neumann eigenvalues with the zero mode set to 0, DCT-III back; Sec. 4, the
+ * phi-subproblem of Algorithm 2).  b, phi: [T+1][N_1]...[N_D] host arrays. */
+int dot_poisson(dot_ctx *ctx, const double *b, double *phi);
+
+/* Per-kernel timing.  dot_profile(ctx, 1) resets the counters and makes every
+ * later launch on this context bracketed by CUDA events recorded on the
+ * context's stream; the elapsed times are accumulated per kernel id at every
+ * synchronisation point (stopping-measure checks, end of dot_solve).
+ * dot_profile(ctx, 0) stops.  dot_profile_read copies, for kernel ids
+ * 0..max-1, the total milliseconds and launch counts; it returns the number of
+ * kernel ids (DOT_NUM_KERNELS).  dot_kernel_name(id) names each id. */
+#define DOT_NUM_KERNELS 12
+int dot_profile(dot_ctx *ctx, int enable);
+int dot_profile_read(dot_ctx *ctx, double *ms_total, long *launches, int max);
+const char *dot_kernel_name(int id);
+
+void dot_destroy(dot_ctx *ctx);
+const char *dot_last_error(const dot_ctx *ctx);
+
+/* Library version string and the number of kernel launches issued by this
+ * context so far (for launch accounting). */
+const char *dot_version(void);
+long dot_launch_count(const dot_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOT_GB300_H */

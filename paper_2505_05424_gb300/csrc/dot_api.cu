@@ -1,0 +1,449 @@
+// dot_api.cu -- the C ABI of include/dot.h: validation, the workspace plan,
+// Algorithm 2's outer loop with the penalty rule and stopping test of Sec. 5.3,
+// and host<->device layout conversion.  All per-element work runs in the kernels
+// of the sibling .cu files; the host only moves scalars and copies buffers.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dot.h"
+#include "dot_internal.cuh"
+#include "dot_paths.cuh"
+
+using namespace dot;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+double elapsed_s(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+bool grid_ok(const dot_grid* g, std::string* why) {
+  if (!g) { *why = "grid is NULL"; return false; }
+  if (g->D != 2 && g->D != 3) { *why = "D must be 2 or 3"; return false; }
+  if (g->T < 1 || g->T > 65535) { *why = "T must be in [1, 65535]"; return false; }
+  long double n = (long double)(g->T + 1);
+  for (int d = 0; d < g->D; ++d) {
+    if (g->N[d] < 2 || g->N[d] > 65536) { *why = "every N[d] must be in [2, 65536]"; return false; }
+    n *= g->N[d];
+  }
+  if (n > 4.0e9L) { *why = "grid too large"; return false; }
+  return true;
+}
+
+}  // namespace
+
+Geo dot::make_geo(const dot_grid& gr) {
+  Geo g;
+  std::memset(&g, 0, sizeof(g));
+  g.D = gr.D;
+  g.T = gr.T;
+  g.K = 4 * gr.D + 2;
+  for (int d = 0; d < kMaxD; ++d) g.N[d] = d < gr.D ? gr.N[d] : 1;
+  long long st = 1;
+  for (int d = gr.D - 1; d >= 0; --d) {
+    g.sst[d] = st;
+    st *= g.N[d];
+  }
+  for (int d = gr.D; d < kMaxD; ++d) g.sst[d] = st;
+  g.P = st;
+  g.invh[0] = (double)gr.T;
+  for (int d = 0; d < gr.D; ++d) g.invh[1 + d] = (double)gr.N[d];
+  return g;
+}
+
+struct dot_ctx {
+  dot_grid grid;
+  dot_options opt;
+  Geo geo;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  std::unique_ptr<Path> path;
+  double* h_red = nullptr;  // pinned R_NSLOTS doubles
+  std::vector<double> m0, m1, omega;
+  double sigma = 1.0;
+  long iters = 0;
+  double kkt[DOT_KKT_LEN];
+  std::string err;
+  long launches = 0;
+  // per-kernel timing (dot_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kid;
+  size_t ev_n = 0;
+  double prof_ms[KID_COUNT] = {0};
+  long prof_cnt[KID_COUNT] = {0};
+};
+
+namespace {
+
+const char* const kKernelNames[KID_COUNT] = {
+    "assemble_b", "dct_axis", "dct_scale", "poisson_residual", "poisson_combine", "cone_project",
+    "update_q0_alpha0", "update_qd_alphad", "update_beta", "kkt_reductions", "dct_tcgen05", "fused_cone_update"};
+
+// Record a CUDA event on the context's stream; kid < 0 marks a start point.
+void prof_record(dot_ctx* c, int kid) {
+  if (c->ev_n == c->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev.push_back(e);
+    c->ev_kid.push_back(-1);
+  }
+  cudaEventRecord(c->ev[c->ev_n], c->stream);
+  c->ev_kid[c->ev_n] = kid;
+  ++c->ev_n;
+}
+
+void prof_mark(void* user, int kid) { prof_record(static_cast<dot_ctx*>(user), kid); }
+
+// After a stream synchronisation: attribute each interval between consecutive
+// events to the kernel launched at its end.
+void prof_flush(dot_ctx* c) {
+  for (size_t i = 1; i < c->ev_n; ++i) {
+    const int kid = c->ev_kid[i];
+    if (kid < 0 || kid >= KID_COUNT) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) {
+      c->prof_ms[kid] += ms;
+      c->prof_cnt[kid] += 1;
+    }
+  }
+  c->ev_n = 0;
+}
+
+LaunchCounter counter(dot_ctx* c) {
+  LaunchCounter lc{&c->launches};
+  if (c->prof) {
+    lc.mark = prof_mark;
+    lc.user = c;
+  }
+  return lc;
+}
+
+int fail(dot_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_thread_err = msg;
+  return code;
+}
+
+int cuda_fail(dot_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, DOT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DOT_CK(ctx, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// Stopping measures from the reduction slots (Sec. 5.3), discrete L2 norms with
+// the space-time cell volume h_0 h_1 ... h_D.
+void finish_kkt(dot_ctx* c, const double* r) {
+  const Geo& g = c->geo;
+  double vol = 1.0 / g.T;
+  for (int d = 0; d < g.D; ++d) vol *= 1.0 / g.N[d];
+  auto L2 = [vol](double s) { return std::sqrt(vol * s); };
+  double cn2 = 0.0;
+  for (double v : c->m0) cn2 += v * v;
+  for (double v : c->m1) cn2 += v * v;
+  const double dn2 = 2.0 * (double)g.T * (double)g.P;
+  const double etaP = L2(r[R_PRIM]) / (1.0 + L2(r[R_APHI]) + L2(r[R_Q]));
+  const double etaD = L2(r[R_DUALRES]) / (1.0 + L2(cn2));
+  const double c1 = L2(r[R_COMP0]) / (1.0 + L2(r[R_ALPHA0]) + L2(r[R_F]));
+  const double c2 = L2(r[R_COMPD]) / (1.0 + L2(r[R_ALPHAB]) + L2(r[R_G]));
+  const double etaC = c1 > c2 ? c1 : c2;
+  const double psoc = L2(r[R_SOCP]) / (1.0 + L2(dn2));
+  const double dsoc = L2(r[R_SOCD]) / (1.0 + L2(r[R_FBB]) + L2(r[R_ALPHA0] + r[R_ALPHAB]));
+  double eta = etaP;
+  if (etaD > eta) eta = etaD;
+  if (etaC > eta) eta = etaC;
+  if (std::isnan(etaD) || std::isnan(etaC) || std::isnan(etaP)) eta = NAN;
+  c->kkt[DOT_KKT_ETA] = eta;
+  c->kkt[DOT_KKT_ETA_P] = etaP;
+  c->kkt[DOT_KKT_ETA_D] = etaD;
+  c->kkt[DOT_KKT_ETA_C] = etaC;
+  c->kkt[DOT_KKT_ETA_P_SOC] = etaP > psoc ? etaP : psoc;
+  c->kkt[DOT_KKT_ETA_D_SOC] = etaD > dsoc ? etaD : dsoc;
+  c->kkt[DOT_KKT_PRIMAL] = r[R_CPHI];
+  c->kkt[DOT_KKT_DUAL] = r[R_DUALOBJ];
+  c->kkt[DOT_KKT_GAP] = std::fabs(r[R_CPHI] - r[R_DUALOBJ]) / (1.0 + std::fabs(r[R_CPHI]) + std::fabs(r[R_DUALOBJ]));
+  c->kkt[DOT_KKT_ITERS] = (double)c->iters;
+  c->kkt[DOT_KKT_SIGMA] = c->sigma;
+}
+
+int compute_kkt(dot_ctx* c) {
+  LaunchCounter lc = counter(c);
+  if (c->prof) prof_record(c, -1);
+  c->path->kkt(c->stream, lc);
+  DOT_CK(c, cudaGetLastError());
+  DOT_CK(c, cudaMemcpyAsync(c->h_red, c->path->red_out(), sizeof(double) * R_NSLOTS, cudaMemcpyDeviceToHost,
+                            c->stream));
+  DOT_CK(c, cudaStreamSynchronize(c->stream));
+  if (c->prof) prof_flush(c);
+  finish_kkt(c, c->h_red);
+  return DOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dot_default_options(dot_options* o) {
+  if (!o) return;
+  o->prec = DOT_MIXED;
+  o->tau = 1.9;
+  o->sigma0 = 1.0;
+  o->s_sigma = 1.25;
+  o->s_r = 2.0;
+  o->check_every = 10;
+  o->obstacle_weight = 1e-6;
+  o->max_seconds = 0.0;
+}
+
+const char* dot_version(void) { return "dot-gb300 0.1 (sm_103a)"; }
+
+size_t dot_workspace_bytes(const dot_grid* grid, dot_precision prec) {
+  std::string why;
+  if (!grid_ok(grid, &why)) return 0;
+  Geo g = make_geo(*grid);
+  return path_workspace_bytes(g, prec);
+}
+
+int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, const uint8_t* mask,
+               const dot_options* opt, void* workspace, size_t workspace_bytes, void* stream, dot_ctx** out) {
+  if (!out) return fail(nullptr, DOT_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (!grid_ok(grid, &why)) return fail(nullptr, DOT_EINVAL, why);
+  if (!rho0 || !rho1) return fail(nullptr, DOT_EINVAL, "rho0/rho1 is NULL");
+  dot_options o;
+  dot_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.tau > 0.0 && o.tau < 2.0)) return fail(nullptr, DOT_EINVAL, "tau must lie in (0, 2)");
+  if (!(o.sigma0 > 0.0 && std::isfinite(o.sigma0))) return fail(nullptr, DOT_EINVAL, "sigma0 must be > 0");
+  if (!(o.s_sigma > 1.0) || !(o.s_r > 1.0)) return fail(nullptr, DOT_EINVAL, "s_sigma and s_r must be > 1");
+  if (o.check_every < 0) return fail(nullptr, DOT_EINVAL, "check_every must be >= 0");
+  if (!(o.obstacle_weight > 0.0 && std::isfinite(o.obstacle_weight)))
+    return fail(nullptr, DOT_EINVAL, "obstacle_weight must be > 0");
+  if (o.prec != DOT_FP64 && o.prec != DOT_MIXED) return fail(nullptr, DOT_EINVAL, "unknown precision");
+
+  std::unique_ptr<dot_ctx> c(new dot_ctx());
+  c->grid = *grid;
+  c->opt = o;
+  c->geo = make_geo(*grid);
+  const Geo& g = c->geo;
+  const long long P = g.P;
+  // densities -> cell masses (eq. (defc)), each normalised to 1
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = 0; i < P; ++i) {
+    if (!std::isfinite(rho0[i]) || !std::isfinite(rho1[i]) || rho0[i] < 0.0 || rho1[i] < 0.0)
+      return fail(nullptr, DOT_EINVAL, "densities must be finite and non-negative");
+    s0 += rho0[i];
+    s1 += rho1[i];
+  }
+  if (!(s0 > 0.0) || !(s1 > 0.0) || !std::isfinite(s0) || !std::isfinite(s1))
+    return fail(nullptr, DOT_EINVAL, "densities must have positive finite mass");
+  c->m0.resize(P);
+  c->m1.resize(P);
+  c->omega.resize(P);
+  bool any_mask = false;
+  for (long long i = 0; i < P; ++i) {
+    c->m0[i] = rho0[i] / s0;
+    c->m1[i] = rho1[i] / s1;
+    const bool ob = mask && mask[i];
+    any_mask = any_mask || ob;
+    c->omega[i] = ob ? o.obstacle_weight : 1.0;
+  }
+  c->stream = (cudaStream_t)stream;
+  size_t need = path_workspace_bytes(g, o.prec);
+  if (workspace) {
+    if (workspace_bytes < need)
+      return fail(nullptr, DOT_ENOMEM, "workspace smaller than dot_workspace_bytes()");
+    if (((uintptr_t)workspace & 255u) != 0) return fail(nullptr, DOT_EINVAL, "workspace must be 256-byte aligned");
+    c->ws = (char*)workspace;
+    c->ws_bytes = workspace_bytes;
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) return fail(nullptr, DOT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->ws = (char*)p;
+    c->ws_bytes = need;
+    c->own_ws = true;
+  }
+  cudaError_t e = cudaMallocHost(&c->h_red, sizeof(double) * R_NSLOTS);
+  if (e != cudaSuccess) {
+    if (c->own_ws) cudaFree(c->ws);
+    return fail(nullptr, DOT_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  }
+  c->path = make_path(o.prec, g);
+  std::string perr;
+  int rc = c->path->init(c->ws, c->ws_bytes, c->m0, c->m1, any_mask ? &c->omega : nullptr, c->stream, &perr);
+  if (rc != DOT_OK) {
+    cudaFreeHost(c->h_red);
+    if (c->own_ws) cudaFree(c->ws);
+    return fail(nullptr, rc, perr);
+  }
+  c->sigma = o.sigma0;
+  c->iters = 0;
+  for (int i = 0; i < DOT_KKT_LEN; ++i) c->kkt[i] = NAN;
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFreeHost(c->h_red);
+    if (c->own_ws) cudaFree(c->ws);
+    return fail(nullptr, DOT_ECUDA, std::string("dot_create: ") + cudaGetErrorString(e));
+  }
+  *out = c.release();
+  return DOT_OK;
+}
+
+int dot_solve(dot_ctx* c, double tol, long maxit) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  if (maxit < 0) return fail(c, DOT_EINVAL, "maxit must be >= 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int ce = c->opt.check_every;
+  LaunchCounter lc = counter(c);
+  for (long k = 1; k <= maxit; ++k) {
+    if (c->prof) {
+      if (c->ev_n > 4096) {
+        DOT_CK(c, cudaStreamSynchronize(c->stream));
+        prof_flush(c);
+      }
+      prof_record(c, -1);
+    }
+    c->path->iterate(c->sigma, c->opt.tau, c->stream, lc);
+    ++c->iters;
+    if (ce > 0 && k % ce == 0) {
+      int rc = compute_kkt(c);
+      if (rc != DOT_OK) return rc;
+      const double eta = c->kkt[DOT_KKT_ETA];
+      if (!std::isfinite(eta)) return fail(c, DOT_EDIVERGED, "stopping measure is not finite");
+      if (tol > 0.0 && eta <= tol) return DOT_OK;
+      // penalty rule (Sec. 5.3) on eta_P^soc / eta_D^soc
+      const double ratio = c->kkt[DOT_KKT_ETA_P_SOC] / c->kkt[DOT_KKT_ETA_D_SOC];
+      if (ratio > c->opt.s_r)
+        c->sigma *= c->opt.s_sigma;
+      else if (ratio < 1.0 / c->opt.s_r)
+        c->sigma /= c->opt.s_sigma;
+      if (c->opt.max_seconds > 0.0 && elapsed_s(t0) > c->opt.max_seconds)
+        return fail(c, DOT_ETIMEOUT, "max_seconds elapsed");
+    }
+  }
+  DOT_CK(c, cudaGetLastError());
+  DOT_CK(c, cudaStreamSynchronize(c->stream));
+  if (c->prof) prof_flush(c);
+  return DOT_ENOTCONV;
+}
+
+int dot_kkt(dot_ctx* c, double* kkt) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  int rc = compute_kkt(c);
+  if (rc != DOT_OK) return rc;
+  if (kkt) std::memcpy(kkt, c->kkt, sizeof(c->kkt));
+  return DOT_OK;
+}
+
+int dot_get(dot_ctx* c, double* rho, double* m, double* phi, double* objective, double* kkt) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  const Geo& g = c->geo;
+  if (objective || kkt) {
+    int rc = compute_kkt(c);
+    if (rc != DOT_OK) return rc;
+    if (objective) *objective = -2.0 * c->kkt[DOT_KKT_PRIMAL];
+    if (kkt) std::memcpy(kkt, c->kkt, sizeof(c->kkt));
+  }
+  std::string perr;
+  int rc = c->path->read_fields(rho, m, phi, c->stream, &perr);
+  if (rc != DOT_OK) return fail(c, rc, perr);
+  const double invh0 = (double)g.T;   // rho = alpha_0 / h_0, m = alpha_bar / h_0
+  if (rho) {
+    const long long n0 = (long long)g.T * g.P;
+    for (long long i = 0; i < n0; ++i) rho[i] *= invh0;
+  }
+  if (m) {
+    long long nm = 0;
+    for (int d = 0; d < g.D; ++d) nm += (long long)(g.T + 1) * g.P / g.N[d] * (g.N[d] - 1);
+    for (long long i = 0; i < nm; ++i) m[i] *= invh0;
+  }
+  return DOT_OK;
+}
+
+int dot_get_state(dot_ctx* c, double* q, double* alpha, double* beta, double* sigma, long* iters) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  std::string perr;
+  int rc = c->path->read_state(q, alpha, beta, c->stream, &perr);
+  if (rc != DOT_OK) return fail(c, rc, perr);
+  if (sigma) *sigma = c->sigma;
+  if (iters) *iters = c->iters;
+  return DOT_OK;
+}
+
+int dot_set_state(dot_ctx* c, const double* q, const double* alpha, const double* beta, double sigma,
+                  long iters) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  if (!q || !alpha || !beta) return fail(c, DOT_EINVAL, "q, alpha and beta are required");
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(c, DOT_EINVAL, "sigma must be > 0");
+  std::string perr;
+  int rc = c->path->write_state(q, alpha, beta, c->stream, &perr);
+  if (rc != DOT_OK) return fail(c, rc, perr);
+  c->sigma = sigma;
+  c->iters = iters;
+  return DOT_OK;
+}
+
+int dot_poisson(dot_ctx* c, const double* b, double* phi) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  if (!b || !phi) return fail(c, DOT_EINVAL, "b and phi are required");
+  std::string perr;
+  LaunchCounter lc = counter(c);
+  if (c->prof) prof_record(c, -1);
+  int rc = c->path->poisson_op(b, phi, c->stream, lc, &perr);
+  if (c->prof) prof_flush(c);
+  if (rc != DOT_OK) return fail(c, rc, perr);
+  return DOT_OK;
+}
+
+int dot_profile(dot_ctx* c, int enable) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DOT_CK(c, cudaStreamSynchronize(c->stream));
+  if (c->prof) prof_flush(c);
+  c->prof = enable != 0;
+  if (c->prof) {
+    for (int i = 0; i < KID_COUNT; ++i) { c->prof_ms[i] = 0.0; c->prof_cnt[i] = 0; }
+    c->ev_n = 0;
+  }
+  return DOT_OK;
+}
+
+int dot_profile_read(dot_ctx* c, double* ms_total, long* launches, int max) {
+  if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  for (int i = 0; i < max && i < KID_COUNT; ++i) {
+    if (ms_total) ms_total[i] = c->prof_ms[i];
+    if (launches) launches[i] = c->prof_cnt[i];
+  }
+  return KID_COUNT;
+}
+
+const char* dot_kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kKernelNames[id] : ""; }
+
+void dot_destroy(dot_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->path.reset();
+  if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  delete c;
+}
+
+const char* dot_last_error(const dot_ctx* c) { return c ? c->err.c_str() : g_thread_err.c_str(); }
+
+long dot_launch_count(const dot_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// dot_internal.cuh -- shared declarations of the CUDA path (kernels + host control).
+//
+// Device layout.  Every field is a stack of time planes of P = N_1 * ... * N_D
+// elements in C order ([x_1]...[x_D], x_D fastest):
+//   nodes (phi, b, Poisson scratch)   : T+1 planes
+//   q_0, alpha_0 (time faces, cones)   : T planes
+//   q_d, alpha_d (space faces, d >= 1) : T+1 planes, padded to N_d entries along
+//                                        axis d; the entry x_d = N_d - 1 is a pad
+//                                        that is kept at exactly 0
+//   beta (and z in the FP64 path)      : K = 4D+2 component planes of T*P each
+// The padding gives every staggered field the node layout, so a stencil reads
+// its neighbours at fixed offsets (P along time, sst[d] along axis d).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dot {
+
+constexpr int kMaxD = 3;
+constexpr int kMaxK = 4 * kMaxD + 2;
+
+// Grid geometry passed by value to every kernel.
+struct Geo {
+  int D;                 // spatial dimension
+  int T;                 // time intervals
+  int K;                 // cone dimension 4D + 2
+  int N[kMaxD];          // cells per spatial axis (1 beyond D)
+  long long P;           // nodes per time plane
+  long long sst[kMaxD];  // element stride of spatial axis d inside a plane
+  double invh[kMaxD + 1];  // 1/h: invh[0] = T, invh[1 + d] = N_d
+};
+
+__device__ __forceinline__ int coord(const Geo& g, long long p, int d) {
+  return (int)((p / g.sst[d]) % g.N[d]);
+}
+
+// Reduction slots of the stopping measures (sums of squares and inner products).
+enum RedSlot {
+  R_PRIM = 0,     // sum (A phi - q)^2
+  R_APHI,         // sum (A phi)^2
+  R_Q,            // sum q^2
+  R_DUALRES,      // sum (A^* alpha + c)^2
+  R_COMP0,        // sum (alpha_0 - max(0, f + alpha_0))^2
+  R_ALPHA0,       // sum alpha_0^2
+  R_F,            // sum f^2
+  R_COMPD,        // sum (alpha_bar - g)^2
+  R_ALPHAB,       // sum alpha_bar^2
+  R_G,            // sum g^2
+  R_SOCP,         // sum (z - B F q - d)^2
+  R_SOCD,         // sum (F^* B^* beta + alpha)^2
+  R_FBB,          // sum (F^* B^* beta)^2
+  R_CPHI,         // <c, phi>
+  R_DUALOBJ,      // -1/2 sum alpha_bar^2 / den over den > 0
+  R_NSLOTS
+};
+
+// FP64 fields (all device pointers into the workspace).
+struct F64Fields {
+  double* q[kMaxD + 1];
+  double* al[kMaxD + 1];
+  double* beta;   // K * T * P
+  double* z;      // K * T * P
+  double* phi;    // (T+1) * P
+  double* b;      // (T+1) * P, also Poisson ping-pong buffer
+  double* w1;     // (T+1) * P Poisson ping-pong buffer
+  const double* m0;      // P, rho0 cell masses
+  const double* m1;      // P, rho1 cell masses
+  const double* omega;   // P or nullptr (omega = 1 everywhere)
+  const double* somega;  // P or nullptr: sqrt(omega / 2)
+};
+
+// DCT tables per axis (axis 0 = time): orthonormal DCT-II matrix (M x M,
+// row k = frequency) and the 1D Neumann eigenvalues (4/h^2) sin^2(pi k / (2M)).
+struct DctTables64 {
+  const double* C[kMaxD + 1];
+  const double* lam[kMaxD + 1];
+};
+
+// ---- launch helpers (defined in the .cu files) ----------------------------
+// Kernel ids for launch accounting and per-kernel timing (names in dot_api.cu).
+enum KernelId {
+  KID_ASSEMBLE_B = 0, KID_DCT_AXIS, KID_SCALE, KID_RESIDUAL, KID_COMBINE, KID_PROJECT,
+  KID_UPDATE_Q0, KID_UPDATE_QD, KID_UPDATE_BETA, KID_KKT, KID_DCT_TC, KID_FUSED, KID_COUNT
+};
+
+// Counts launches; when `mark` is set, it is called after every launch with the
+// kernel id so the caller can record a CUDA event on the launching stream.
+struct LaunchCounter {
+  long* n;
+  void (*mark)(void*, int) = nullptr;
+  void* user = nullptr;
+  void tick(int k = 1) const { if (n) *n += k; }
+  void launched(int kid, int k = 1) const {
+    tick(k);
+    if (mark) mark(user, kid);
+  }
+};
+
+void launch_assemble_b_f64(const Geo& g, const F64Fields& f, double sigma, cudaStream_t s, LaunchCounter lc);
+void launch_project_f64(const Geo& g, const F64Fields& f, double sigma, cudaStream_t s, LaunchCounter lc);
+void launch_update_q_alpha_f64(const Geo& g, const F64Fields& f, double sigma, double tau, cudaStream_t s, LaunchCounter lc);
+void launch_update_beta_f64(const Geo& g, const F64Fields& f, double sigma, double tau, cudaStream_t s, LaunchCounter lc);
+// Poisson solve in place of (b -> phi), using w1 as scratch.  b is overwritten.
+void launch_poisson_f64(const Geo& g, const DctTables64& t, double* b, double* w1, double* phi,
+                        cudaStream_t s, LaunchCounter lc);
+// Stopping-measure sums into out[R_NSLOTS] (device), using `partials` scratch of
+// kkt_partials_len(g) doubles.
+long long kkt_partials_len(const Geo& g);
+void launch_kkt_f64(const Geo& g, const F64Fields& f, double* partials, double* out, cudaStream_t s,
+                    LaunchCounter lc);
+
+}  // namespace dot

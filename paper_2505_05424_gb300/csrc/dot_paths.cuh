@@ -1,0 +1,63 @@
+// dot_paths.cuh -- one implementation of Algorithm 2 per precision mode behind a
+// small interface used by the C ABI layer (dot_api.cu).
+#pragma once
+#include <cstddef>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dot.h"
+#include "dot_internal.cuh"
+
+namespace dot {
+
+Geo make_geo(const dot_grid& gr);
+
+// Bump allocator over the caller's workspace; with base == nullptr it only
+// measures (used by dot_workspace_bytes).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+class Path {
+ public:
+  virtual ~Path() {}
+  // Carve buffers, upload masses/omega/DCT tables, zero the iterate.
+  virtual int init(char* ws, size_t bytes, const std::vector<double>& m0, const std::vector<double>& m1,
+                   const std::vector<double>* omega, cudaStream_t s, std::string* err) = 0;
+  // One iteration of Algorithm 2 (lines 1-6) with penalty sigma and step tau.
+  virtual void iterate(double sigma, double tau, cudaStream_t s, LaunchCounter lc) = 0;
+  // Stopping-measure sums into red_out() (device, R_NSLOTS doubles).
+  virtual void kkt(cudaStream_t s, LaunchCounter lc) = 0;
+  virtual const double* red_out() const = 0;
+  // alpha_0 (natural layout) into rho, alpha_bar (natural layout) into m, phi; NULL = skip.
+  virtual int read_fields(double* rho, double* m, double* phi, cudaStream_t s, std::string* err) = 0;
+  virtual int read_state(double* q, double* al, double* beta, cudaStream_t s, std::string* err) = 0;
+  virtual int write_state(const double* q, const double* al, const double* beta, cudaStream_t s,
+                          std::string* err) = 0;
+  virtual int poisson_op(const double* b, double* phi, cudaStream_t s, LaunchCounter lc, std::string* err) = 0;
+};
+
+size_t path_workspace_bytes(const Geo& g, dot_precision prec);
+std::unique_ptr<Path> make_path(dot_precision prec, const Geo& g);
+// The mixed-precision path (path_mixed.cu).
+void carve_mixed_size(const Geo& g, Carver& cv);
+std::unique_ptr<Path> make_mixed_path(const Geo& g);
+
+// Shared host helpers (defined in path_f64.cu).
+void dct_tables_host(const Geo& g, int axis, std::vector<double>* C, std::vector<double>* lam);
+// Geometry of face family fam >= 1 for the natural <-> padded copies:
+// width / pitch in elements, height in rows.
+void face_copy_shape(const Geo& g, int fam, size_t* width, size_t* pitch, size_t* height);
+long long natural_face_count(const Geo& g, int fam);
+
+}  // namespace dot

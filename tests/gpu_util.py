@@ -1,0 +1,33 @@
+"""Helpers shared by the GPU parity tests: build the library once, pair a GPU
+solver with the oracle on identical seeded inputs, and convert layouts."""
+import numpy as np
+
+import oracle as O
+from paper_2505_05424_gb300 import _native as N
+from paper_2505_05424_gb300.solver import DotSolver
+
+
+def ensure_built():
+    N.build()
+    return N.load()
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    den = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / den)
+
+
+def pair(D, T, N_, r0, r1, mask=None, prec="fp64", **opts):
+    g = O.Grid(D, T, N_)
+    prob = O.Problem(g, r0, r1, mask)
+    gpu = DotSolver(D, T, N_, r0, r1, mask=mask, prec=prec, **opts)
+    return g, prob, gpu
+
+
+def random_state(g, rng, scale=1.0):
+    """A random iterate (q, alpha, beta) in the oracle's natural layout."""
+    q = rng.standard_normal(g.n_q) * scale
+    al = rng.standard_normal(g.n_q) * scale * 0.1
+    beta = rng.standard_normal(g.K * g.n_cones) * scale
+    return q, al, beta

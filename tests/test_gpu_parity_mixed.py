@@ -1,0 +1,108 @@
+"""GPU parity of the mixed-precision path against the FP64 oracle.
+
+Tolerances come from the arithmetic.  One step: FP32 unit roundoff u = 6e-8;
+each output is the end of at most ~20 roundings with an amplification of at most
+~10 (the divisions in the cone projection and the diagonal solve), so a step
+agrees to 2e-5 relative to the field's maximum.  The refined Poisson solve
+(FP32 solve, exact two-float residual, FP32 correction) is accurate to u^2 times
+the conditioning of the DCT pair, tested at 1e-9.  Whole solves: KKT <= 1e-6 and
+the objective against the FP64 oracle's continued to eta <= 1e-7.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import ensure_built, pair, random_state, rel_err
+from paper_2505_05424_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+GRIDS = [(2, 4, [6, 5]), (2, 1, [2, 2]), (2, 69, [70, 3]), (2, 7, [9, 131]), (3, 3, [4, 3, 5]),
+         (3, 5, [6, 7, 66])]
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("D,T,N", GRIDS)
+def test_refined_poisson(D, T, N):
+    rng = np.random.default_rng(500 + T)
+    g = O.Grid(D, T, N)
+    b = f32(rng.standard_normal(g.n_nodes) + 0.5)
+    r0 = rng.random(int(np.prod(N))) + 0.1
+    _, _, gpu = pair(D, T, N, r0, r0, prec="mixed")
+    phi = gpu.dot_poisson(b)
+    ref = O.poisson(g, b)
+    assert rel_err(phi, ref) < 1e-9
+    gpu.close()
+
+
+@pytest.mark.parametrize("D,T,N", GRIDS)
+@pytest.mark.parametrize("masked", [False, True])
+def test_one_iteration_from_random_state(D, T, N, masked):
+    rng = np.random.default_rng(600 + T + 7 * masked)
+    P = int(np.prod(N))
+    r0, r1 = rng.random(P) + 0.05, rng.random(P) + 0.05
+    mask = (rng.random(P) < 0.2) if masked else None
+    g, prob, gpu = pair(D, T, N, r0, r1, mask=mask, prec="mixed", check_every=0)
+    q, al, beta = random_state(g, rng)
+    q = f32(q)                      # q is stored in FP32 on the GPU
+    sigma = float(rng.uniform(0.5, 3.0))
+    st = O.State(g, np.zeros(g.n_nodes), np.zeros(g.K * g.n_cones), q.copy(), al.copy(), beta.copy(), sigma)
+    O.iterate(prob, st, tau=1.9)
+    gpu.dot_set_state(q, al, beta, sigma)
+    gpu.dot_solve(tol=0.0, maxit=1)
+    q2, al2, b2, _, it = gpu.dot_get_state()
+    _, _, phi, _, _ = gpu.dot_get()
+    assert it == 1
+    assert rel_err(phi.ravel(), st.phi) < STEP_TOL
+    assert rel_err(q2, st.q) < STEP_TOL
+    assert rel_err(al2, st.alpha) < STEP_TOL
+    assert rel_err(b2, st.beta) < STEP_TOL
+    kg, ko = gpu.dot_kkt(), O.kkt(prob, st)
+    for name in ("eta_P", "eta_D", "eta_C", "eta_P_soc", "eta_D_soc"):
+        assert abs(kg[name] - ko[name]) <= 1e-3 * abs(ko[name]) + 1e-7, name
+    assert abs(kg["primal_obj"] - ko["primal_obj"]) <= STEP_TOL * max(abs(ko["primal_obj"]), 1e-12)
+    gpu.close()
+
+
+def test_gauss32_mixed_converges_to_fp64_objective():
+    """2D 32^2 x 16 two Gaussians + floor: mixed reaches KKT 1e-6 and matches the
+    FP64 oracle's objective (continued to eta <= 1e-7) and densities."""
+    spec, r0, r1, mask = W.workload("gauss32")
+    g, prob, gpu = pair(2, spec.T, [spec.N] * 2, r0, r1, prec="mixed")
+    st = O.State.zeros(g)
+    res = O.solve(prob, st, tol=1e-7, maxit=60000)
+    rc = gpu.dot_solve(tol=1e-6, maxit=20000)
+    assert rc == 0
+    rho, m, phi, obj, kk = gpu.dot_get()
+    assert kk["eta_dot"] <= 1e-6
+    ref = -2 * res["primal_obj"]
+    print("mixed iters", kk["iterations"], "obj", obj, "ref", ref, "rel", abs(obj - ref) / abs(ref),
+          "max|rho-rho_o|", np.abs(rho - O.density_slices(g, st)).max())
+    assert abs(obj - ref) <= 1e-5 * abs(ref)
+    assert np.abs(rho - O.density_slices(g, st)).max() <= 1e-3 * np.abs(rho).max()
+    gpu.close()
+
+
+def test_mixed_lockstep_tracks_fp64():
+    """Tens of iterations: the mixed iterate stays within the FP32 noise of the oracle's."""
+    rng = np.random.default_rng(700)
+    r0, r1 = rng.random(120) + 0.05, rng.random(120) + 0.05
+    g, prob, gpu = pair(2, 8, [12, 10], r0, r1, prec="mixed", check_every=10)
+    st = O.State.zeros(g)
+    O.solve(prob, st, tol=0.0, maxit=50, check_every=10)
+    gpu.dot_solve(tol=0.0, maxit=50)
+    q2, al2, b2, s2, _ = gpu.dot_get_state()
+    assert s2 == st.sigma
+    assert rel_err(q2, st.q) < 1e-4 and rel_err(al2, st.alpha) < 1e-4 and rel_err(b2, st.beta) < 1e-4
+    gpu.close()
