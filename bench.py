@@ -205,7 +205,7 @@ def run_ours(args):
         kk = s.dot_kkt()
         iters.append(int(kk["iterations"]))
         etas.append(kk["eta_dot"])
-        objs.append(-2.0 * kk["primal_obj"])
+        objs.append(-2.0 * kk["primal_obj"] / spec.N ** spec.D)   # W2^2 = -2 |X_i| <c, phi>
         if rc != 0:
             print(json.dumps({"warning": f"solve did not converge (rc={rc})", "eta": kk["eta_dot"]}),
                   file=sys.stderr)
@@ -316,7 +316,7 @@ def run_ours(args):
         out["fp64"] = {"solves_per_s": (1.0 / dt) if rc == 0 else None, "seconds": round(dt, 3),
                        "iterations": fp64_iters, "eta_dot": kk["eta_dot"], "converged": rc == 0,
                        "ms_per_iter": round(dt * 1e3 / max(fp64_iters, 1), 3),
-                       "objective": -2.0 * kk["primal_obj"]}
+                       "objective": -2.0 * kk["primal_obj"] / spec.N ** spec.D}
         if rc == 0:
             out["mixed_vs_fp64"] = round(value / (1.0 / dt), 3)
 

@@ -80,7 +80,7 @@ enum {
   DOT_KKT_ETA_C = 3,
   DOT_KKT_ETA_P_SOC = 4,
   DOT_KKT_ETA_D_SOC = 5,
-  DOT_KKT_PRIMAL = 6,     /* <c, phi>, the objective of problem (8) */
+  DOT_KKT_PRIMAL = 6,     /* <c, phi>, the objective of problem (8), c in densities */
   DOT_KKT_DUAL = 7,       /* dual objective (11) at the current alpha */
   DOT_KKT_GAP = 8,        /* |primal - dual| / (1 + |primal| + |dual|) */
   DOT_KKT_ITERS = 9,      /* iterations run since dot_create / dot_set_state */
@@ -118,9 +118,11 @@ int dot_create(const dot_grid *grid, const double *rho0, const double *rho1,
 int dot_solve(dot_ctx *ctx, double tol, long maxit);
 
 /* Results.  Any pointer may be NULL.  rho = alpha_0 / h_0 and m_d = alpha_d / h_0
- * (Proposition 3.3: (Lambda_0, Lambda_bar) = (alpha_0, alpha_bar) solve (12));
- * objective = -2 <c, phi> (the squared Wasserstein-2 distance of the discrete
- * problem); kkt: DOT_KKT_LEN values measured at the current iterate. */
+ * (Proposition 3.3: (Lambda_0, Lambda_bar) = (alpha_0, alpha_bar) solve (12)), as
+ * densities: each time slice of rho integrates to 1, sum(rho) * h_1...h_D = 1.
+ * c enters eq. (defc) as cell-average densities (mass / h_1...h_D), so
+ * objective = -2 h_1...h_D <c, phi>, the squared Wasserstein-2 distance of the
+ * discrete problem; kkt: DOT_KKT_LEN values measured at the current iterate. */
 int dot_get(dot_ctx *ctx, double *rho, double *m, double *phi, double *objective, double *kkt);
 
 /* Stopping measures of the current iterate (Sec. 5.3) into kkt[DOT_KKT_LEN]. */

@@ -214,6 +214,7 @@ def fill_d(g: Grid):
 
 
 def fill_c(g: Grid, m0, m1):
+    """c of eq. (defc) from cell masses, as cell-average densities (see og_fill_c)."""
     m0, m1 = _f64(m0).ravel(), _f64(m1).ravel()
     out = np.zeros(g.n_nodes)
     _load().og_fill_c(g.ref, _ptr(m0), _ptr(m1), _ptr(out))
@@ -350,8 +351,20 @@ def solve(prob: Problem, st: State, tol: float = 1e-6, maxit: int = 100000, tau:
 
 
 def density_slices(g: Grid, st: State) -> np.ndarray:
-    """rho on G^s_0 as mass per cell per time slice: alpha_0 / h_0 (Proposition 3.3)."""
+    """rho on G^s_0 as a density (mass per unit area) per time slice: alpha_0 / h_0
+    (Proposition 3.3; c carries densities, see og_fill_c).  Each slice integrates
+    to sum(rho) * cell_area = 1."""
     return st.alpha[: g.n_cones].reshape((g.T,) + g.N) * g.T
+
+
+def cell_area(g: Grid) -> float:
+    """|X_i| = h_1 ... h_D, the spatial cell volume."""
+    return float(np.prod([1.0 / n for n in g.N]))
+
+
+def w2_squared(g: Grid, primal_obj: float) -> float:
+    """Squared W2 of the discrete problem from <c, phi>: -2 |X_i| <c, phi>."""
+    return -2.0 * cell_area(g) * primal_obj
 
 
 def momentum(g: Grid, st: State):

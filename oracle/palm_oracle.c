@@ -385,14 +385,23 @@ void og_poisson(const og_grid *g, const double *b, double *phi) {
 
 /* ---- problem data c (eq. (defc)) ---------------------------------------- */
 
-/* c = rho0 masses on the i_0 = 0 slice, -rho1 masses on i_0 = n_0, 0 elsewhere. */
+/* c of eq. (defc): rho0 on the i_0 = 0 slice, -rho1 on i_0 = n_0, 0 elsewhere.
+ * m0, m1 are cell masses (each summing to 1).  The data enter as cell-average
+ * densities, mass / |X_i| with |X_i| = h_1 ... h_D: the initial data are scaled
+ * (Sec. 5.3) so that the densities are O(1), the scale on which the uniform lower
+ * bounds delta of Sec. 5.4's examples are stated.  The scaling multiplies the
+ * objective and the multipliers by 1/|X_i| and leaves phi and q unchanged; without
+ * it the volume-weighted L2 norms of A^*alpha + c and of alpha are O(|X_i|) and
+ * eta_dot is meaningless on fine grids. */
 void og_fill_c(const og_grid *g, const double *m0, const double *m1, double *c) {
   og_shape sn = og_shape_of(g, -1);
   long P = sn.st[0];
+  double inv_cell = 1.0;
+  for (int d = 1; d <= g->D; ++d) inv_cell *= (double)g->N[d - 1];   /* 1 / (h_1 ... h_D) */
   memset(c, 0, sizeof(double) * sn.size);
   for (long p = 0; p < P; ++p) {
-    c[p] = m0[p];
-    c[(long)g->T * P + p] = -m1[p];
+    c[p] = m0[p] * inv_cell;
+    c[(long)g->T * P + p] = -m1[p] * inv_cell;
   }
 }
 

@@ -33,7 +33,9 @@ bool grid_ok(const dot_grid* g, std::string* why) {
     if (g->N[d] < 2 || g->N[d] > 65536) { *why = "every N[d] must be in [2, 65536]"; return false; }
     n *= g->N[d];
   }
-  if (n > 4.0e9L) { *why = "grid too large"; return false; }
+  // every field's element index, including 4D+2 stacked cone components, stays
+  // below 2^31 (32-bit index arithmetic in the kernels)
+  if (n * (long double)(4 * g->D + 2) >= 2147483648.0L) { *why = "grid too large"; return false; }
   return true;
 }
 
@@ -55,6 +57,11 @@ Geo dot::make_geo(const dot_grid& gr) {
   g.P = st;
   g.invh[0] = (double)gr.T;
   for (int d = 0; d < gr.D; ++d) g.invh[1 + d] = (double)gr.N[d];
+  g.fP = make_fastdiv((unsigned)g.P);
+  for (int d = 0; d < kMaxD; ++d) {
+    g.fS[d] = make_fastdiv((unsigned)g.sst[d]);
+    g.fN[d] = make_fastdiv((unsigned)g.N[d]);
+  }
   return g;
 }
 
@@ -67,7 +74,7 @@ struct dot_ctx {
   size_t ws_bytes = 0;
   bool own_ws = false;
   std::unique_ptr<Path> path;
-  double* h_red = nullptr;  // pinned R_NSLOTS doubles
+  double* h_red = nullptr;  // pinned R_NSLOTS doubles + one int (device error flag)
   std::vector<double> m0, m1, omega;
   double sigma = 1.0;
   long iters = 0;
@@ -185,8 +192,13 @@ int compute_kkt(dot_ctx* c) {
   DOT_CK(c, cudaGetLastError());
   DOT_CK(c, cudaMemcpyAsync(c->h_red, c->path->red_out(), sizeof(double) * R_NSLOTS, cudaMemcpyDeviceToHost,
                             c->stream));
+  int* hflag = reinterpret_cast<int*>(c->h_red + R_NSLOTS);
+  *hflag = 0;
+  if (c->path->error_flag())
+    DOT_CK(c, cudaMemcpyAsync(hflag, c->path->error_flag(), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   DOT_CK(c, cudaStreamSynchronize(c->stream));
   if (c->prof) prof_flush(c);
+  if (*hflag) return fail(c, DOT_ECUDA, "a tensor-core pipeline wait timed out (kernel returned early)");
   finish_kkt(c, c->h_red);
   return DOT_OK;
 }
@@ -254,9 +266,12 @@ int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, con
   c->m1.resize(P);
   c->omega.resize(P);
   bool any_mask = false;
+  // c of eq. (defc) as cell-average densities: mass / (h_1 ... h_D) (the data scaling
+  // of Sec. 5.3; it leaves phi and q unchanged and makes alpha_0 / h_0 the density)
+  const double inv_cell = (double)P;
   for (long long i = 0; i < P; ++i) {
-    c->m0[i] = rho0[i] / s0;
-    c->m1[i] = rho1[i] / s1;
+    c->m0[i] = rho0[i] / s0 * inv_cell;
+    c->m1[i] = rho1[i] / s1 * inv_cell;
     const bool ob = mask && mask[i];
     any_mask = any_mask || ob;
     c->omega[i] = ob ? o.obstacle_weight : 1.0;
@@ -277,7 +292,7 @@ int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, con
     c->ws_bytes = need;
     c->own_ws = true;
   }
-  cudaError_t e = cudaMallocHost(&c->h_red, sizeof(double) * R_NSLOTS);
+  cudaError_t e = cudaMallocHost(&c->h_red, sizeof(double) * (R_NSLOTS + 1));
   if (e != cudaSuccess) {
     if (c->own_ws) cudaFree(c->ws);
     return fail(nullptr, DOT_ENOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
@@ -355,7 +370,7 @@ int dot_get(dot_ctx* c, double* rho, double* m, double* phi, double* objective, 
   if (objective || kkt) {
     int rc = compute_kkt(c);
     if (rc != DOT_OK) return rc;
-    if (objective) *objective = -2.0 * c->kkt[DOT_KKT_PRIMAL];
+    if (objective) *objective = -2.0 * c->kkt[DOT_KKT_PRIMAL] / (double)c->geo.P;
     if (kkt) std::memcpy(kkt, c->kkt, sizeof(c->kkt));
   }
   std::string perr;

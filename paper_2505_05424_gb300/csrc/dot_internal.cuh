@@ -19,7 +19,40 @@ namespace dot {
 constexpr int kMaxD = 3;
 constexpr int kMaxK = 4 * kMaxD + 2;
 
-// Grid geometry passed by value to every kernel.
+// Unsigned division of n < 2^31 by a fixed divisor d >= 2 with one multiply-high
+// and a shift: with l = ceil(log2 d) and m = ceil(2^(31 + l) / d) (< 2^32),
+// floor(n / d) = umulhi(n, m) >> (l - 1) (the round-up method of Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI 1994).
+// d = 1 passes n through.
+struct FastDiv {
+  unsigned d;
+  unsigned m;
+  unsigned sh;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  if (d <= 1) {
+    f.m = 0;
+    f.sh = 0;
+    return f;
+  }
+  unsigned l = 0;
+  while ((1ull << l) < d) ++l;                 // l = ceil(log2 d)
+  const unsigned long long p = 31ull + l;
+  f.m = (unsigned)(((1ull << p) + d - 1) / d);  // ceil(2^p / d) < 2^32
+  f.sh = (unsigned)(p - 32);
+  return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+  return f.d <= 1 ? n : (__umulhi(n, f.m) >> f.sh);
+}
+
+// Grid geometry passed by value to every kernel.  Element indices of one field
+// stay below 2^31 ((T+1) * P * ... is checked at dot_create), so the plane and
+// coordinate arithmetic runs on 32-bit fast divisions.
 struct Geo {
   int D;                 // spatial dimension
   int T;                 // time intervals
@@ -28,11 +61,20 @@ struct Geo {
   long long P;           // nodes per time plane
   long long sst[kMaxD];  // element stride of spatial axis d inside a plane
   double invh[kMaxD + 1];  // 1/h: invh[0] = T, invh[1 + d] = N_d
+  FastDiv fP;            // division by P
+  FastDiv fS[kMaxD];     // division by sst[d]
+  FastDiv fN[kMaxD];     // division by N[d]
 };
 
+// coordinate along spatial axis d of in-plane index p: (p / sst[d]) % N[d]
 __device__ __forceinline__ int coord(const Geo& g, long long p, int d) {
-  return (int)((p / g.sst[d]) % g.N[d]);
+  const unsigned q = fdiv((unsigned)p, g.fS[d]);
+  if (d == 0) return (int)q;   // p < P: the outermost coordinate needs no modulo
+  return (int)(q - fdiv(q, g.fN[d]) * (unsigned)g.N[d]);
 }
+
+// time plane of element index i (i < 2^31)
+__device__ __forceinline__ int plane_of(const Geo& g, long long i) { return (int)fdiv((unsigned)i, g.fP); }
 
 // Reduction slots of the stopping measures (sums of squares and inner products).
 enum RedSlot {

@@ -10,13 +10,15 @@ struct MxFields {
   float2* beta;            // K * T * P two-float multipliers
   float* z;                // K * T * P
   float2* phi;             // (T+1)*P two-float potential
-  float* b;                // (T+1)*P right-hand side; reused for the correction delta
+  float* b;                // (T+1)*P right-hand side, high part; reused for the correction delta
+  float* blo;              // (T+1)*P right-hand side, low part (b = b + blo as a two-float)
   float* phi1;             // (T+1)*P first Poisson solve
   float* r;                // (T+1)*P refinement residual
-  const float* m0f;        // P masses (FP32, for b)
-  const float* m1f;
-  const double* m0;        // P masses (FP64, for the reductions)
-  const double* m1;
+  double* bsum;            // 304 FP64 partial sums of b (zero mode of the right-hand side)
+  const float2* c0;        // P: c on the first time plane (densities, two-float)
+  const float2* c1;        // P: -c on the last time plane (rho1 densities, two-float)
+  const double* m0;        // P: rho0 densities (FP64, for the reductions)
+  const double* m1;        // P: rho1 densities
   const float* omega;      // P or nullptr
   const float* somega;     // P or nullptr: sqrt(omega/2)
 };
@@ -24,11 +26,21 @@ struct MxFields {
 // Poisson solver of the mixed path: per-axis DCT matrices (FP32, and their
 // TF32 hi/lo split for the tensor-core GEMMs), 1D eigenvalues, scratch.
 struct MxPoisson {
-  const float* C[kMaxD + 1];      // M x M, row k = frequency
-  const float* lam[kMaxD + 1];    // M
+  const float* C[kMaxD + 1];      // M x M orthonormal DCT-II, row k = frequency
+  const float* CT[kMaxD + 1];     // its transpose (DCT-III)
+  const float* Chi[kMaxD + 1];    // TF32 split of C: C = Chi + Clo
+  const float* Clo[kMaxD + 1];
+  const float* CThi[kMaxD + 1];   // TF32 split of C^T
+  const float* CTlo[kMaxD + 1];
+  const float* lam[kMaxD + 1];    // M, 1D Neumann eigenvalues
   float* w1;                      // (T+1)*P scratch
   float* w2;                      // (T+1)*P scratch
+  int* err;                       // set by a tensor-core pass whose pipeline wait timed out
+  bool use_tc;                    // run eligible spatial passes on the tensor cores
 };
+
+// Shared memory of the fused time-axis pass (C_t and two 64-column tiles).
+size_t tsolve_smem_bytes(const Geo& g);
 
 // src -> dst (src is preserved), FP32 in and out.
 void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
@@ -38,8 +50,18 @@ void launch_poisson_refined_mx(const Geo& g, const MxFields& f, const MxPoisson&
                                cudaStream_t s, LaunchCounter lc);
 void launch_iterate_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, double sigma, double tau,
                        cudaStream_t s, LaunchCounter lc);
-void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, cudaStream_t s,
-                   LaunchCounter lc);
+// Stopping-measure sums.  socp_part (nullable): per-block sums of |z - BFq - d|^2
+// written by the fused kernel; when given, they replace the z-based term.
+void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
+                   int nsocp, cudaStream_t s, LaunchCounter lc);
+void launch_assemble_b_mx(const Geo& g, const MxFields& f, double sigma, cudaStream_t s, LaunchCounter lc);
+
+// Fused lines 3-6 for D = 2 (k_fused2d.cu): reads q, alpha, beta of f, writes
+// those of fn; phi, somega from f.  socp_part: fused2d_blocks(g) doubles.
+bool fused2d_supported(const Geo& g);
+long long fused2d_blocks(const Geo& g);
+void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
+                    double* socp_part, cudaStream_t s, LaunchCounter lc);
 long long kkt_partials_len_mx(const Geo& g);
 
 }  // namespace dot

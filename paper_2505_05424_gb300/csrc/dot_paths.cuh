@@ -45,6 +45,10 @@ class Path {
   virtual int write_state(const double* q, const double* al, const double* beta, cudaStream_t s,
                           std::string* err) = 0;
   virtual int poisson_op(const double* b, double* phi, cudaStream_t s, LaunchCounter lc, std::string* err) = 0;
+  // Device flag that a kernel sets when a bounded pipeline wait gave up (or nullptr).
+  virtual const int* error_flag() const { return nullptr; }
+  // Mixed path: whether eligible DCT passes run on the tensor cores.
+  virtual void set_tensor_cores(bool) {}
 };
 
 size_t path_workspace_bytes(const Geo& g, dot_precision prec);

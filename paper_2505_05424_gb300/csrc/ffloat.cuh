@@ -55,4 +55,92 @@ __device__ __forceinline__ float2 ff_sub_exact(float a, float b) { return two_su
 
 __device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
 
+// host or device: split a double into (hi, lo) floats
+__host__ __device__ inline float2 ff_from_double(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// exact product of two floats as an ff (TwoProd via FMA)
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+  const float p = a * b;
+  return make_float2(p, fmaf(a, b, -p));
+}
+
+// ff * ff
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  return quick_two_sum(p, e);
+}
+
+// ff^2
+__device__ __forceinline__ float2 ff_sqr(float2 a) {
+  const float p = a.x * a.x;
+  float e = fmaf(a.x, a.x, -p);
+  e = fmaf(2.f * a.x, a.y, e);
+  return quick_two_sum(p, e);
+}
+
+// sqrt of a non-negative ff: FP32 root plus one Newton correction
+__device__ __forceinline__ float2 ff_sqrt(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = sqrtf(a.x);
+  const float2 s2 = two_prod(s, s);
+  const float r = ((a.x - s2.x) - s2.y) + a.y;   // a - s^2, small
+  return quick_two_sum(s, r / (2.f * s));
+}
+
+// ff / ff (b != 0): FP32 quotient plus one correction
+__device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
+  const float q1 = a.x / b.x;
+  const float2 p = ff_mul(make_float2(q1, 0.f), b);
+  const float2 r = ff_add(a, ff_neg(p));
+  const float q2 = r.x / b.x;
+  return quick_two_sum(q1, q2);
+}
+
+// ff / float
+__device__ __forceinline__ float2 ff_div_f(float2 a, float b) {
+  const float q1 = a.x / b;
+  const float2 p = two_prod(q1, b);
+  const float r = ((a.x - p.x) - p.y) + a.y;
+  return quick_two_sum(q1, r / b);
+}
+
+// a <= b for ff values
+__device__ __forceinline__ bool ff_le(float2 a, float2 b) {
+  return a.x < b.x || (a.x == b.x && a.y <= b.y);
+}
+
+__device__ __forceinline__ float ff_round(float2 a) { return a.x + a.y; }
+
+// Projection onto the second-order cone {y_0 >= |ybar|} (eq. (app-proj)) in
+// two-float arithmetic.  The input of the ALM projection is dominated by
+// -beta/sigma, often 10^2 - 10^3 times the O(1) point it projects to, so the
+// boundary case (y_0 + |ybar|)/2 cancels; two-float arithmetic keeps ~2^-44
+// relative accuracy there.  Case order: y if |ybar| <= y_0; 0 if |ybar| <= -y_0;
+// else the boundary formula.
+template <int K>
+__device__ __forceinline__ void ff_proj_soc(float2* y) {
+  float2 nb2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 1; j < K; ++j) nb2 = ff_add(nb2, ff_sqr(y[j]));
+  const float2 nb = ff_sqrt(nb2);
+  if (ff_le(nb, y[0])) return;
+  if (ff_le(nb, ff_neg(y[0]))) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) y[j] = make_float2(0.f, 0.f);
+    return;
+  }
+  const float2 sum = ff_add(y[0], nb);
+  const float2 a = make_float2(0.5f * sum.x, 0.5f * sum.y);
+  const float2 sc = ff_div(a, nb);
+  y[0] = a;
+#pragma unroll
+  for (int j = 1; j < K; ++j) y[j] = ff_mul(sc, y[j]);
+}
+
 }  // namespace dot

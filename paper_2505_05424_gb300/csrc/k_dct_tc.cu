@@ -1,0 +1,387 @@
+// k_dct_tc.cu -- one DCT pass of the mixed-path Poisson solve on the 5th-generation
+// tensor cores (tcgen05, TMEM accumulators, TMA operand staging), in 3xTF32
+// split precision with FP32 accumulation.
+//
+// A pass applies the M x M matrix B (the orthonormal DCT-II matrix C for a forward
+// transform, C^T for the inverse) along the innermost axis of a field stored as
+// [A][Bd][K] (K = M innermost):
+//     Out(k, a, b) = sum_j X(a, b, j) B(k, j)
+// and writes the result with the transformed axis moved outermost, so that the
+// next axis becomes the innermost one and every pass is a K-major GEMM:
+//   mode ROWS_FLAT  tile rows r = a*Bd + b (128 consecutive r); Out[k][r]
+//   mode ROWS_A     tile rows = 128 consecutive a at fixed b;   Out[b][k][a]
+// In both modes the 32 lanes of a warp hold 32 consecutive output addresses for
+// every column k, so the epilogue stores are coalesced.
+//
+// 3xTF32: x = x_hi + x_lo with x_hi = tf32_rna(x) and x_lo = x - x_hi (exact in
+// FP32); B likewise (split once on the host).  Each K-step issues
+// x_hi*B_hi + x_hi*B_lo + x_lo*B_hi into one FP32 accumulator; the dropped
+// x_lo*B_lo term and the truncation of x_lo to TF32 are O(2^-22) relative.
+//
+// CTA roles (192 threads): warp 0 issues TMA loads (one elected lane), warp 1
+// owns TMEM and issues the MMAs (one elected lane), warps 2-5 split the X tile
+// into hi/lo in shared memory and run the epilogue (tcgen05.ld from TMEM).
+// Every mbarrier wait is bounded; on timeout the CTA records the failure in
+// *err, stops issuing work, and still frees its TMEM.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "dot_internal.cuh"
+#include "dot_tc.cuh"
+
+namespace dot {
+namespace {
+
+constexpr int kTileM = 128;          // rows per CTA (MMA M)
+constexpr int kChunkK = 32;          // K elements per stage (128 bytes: one SW128 row)
+constexpr int kStages = 2;
+constexpr int kMaxN = 256;           // columns of the accumulator (MMA N)
+constexpr int kThreadsTC = 192;
+constexpr unsigned kSpinLimit = 1u << 25;   // bounded mbarrier waits (well under a second of polling)
+
+constexpr int kXBytes = kTileM * kChunkK * 4;      // 16 KB
+constexpr int kBBytes = kMaxN * kChunkK * 4;       // 32 KB (one of hi/lo)
+constexpr int kStageBytes = 2 * kXBytes + 2 * kBBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_u32(bar);
+  for (unsigned it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B
+// apart (SBO), LBO unused for this layout (set to 16 B), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                 // LBO (ignored for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+struct PassArgs {
+  float* out;
+  int K;           // length of the transformed axis (= reduction length)
+  int Nout;        // output frequencies computed (MMA N, multiple of 16, <= 256)
+  int Kvalid;      // valid output columns written (= K)
+  int mode;        // 0 = ROWS_FLAT, 1 = ROWS_A
+  long long R;     // ROWS_FLAT: total rows
+  int A, Bd;       // ROWS_A: extents of a and b
+  int* err;
+};
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_bhi,
+              const __grid_constant__ CUtensorMap tm_blo, PassArgs pa) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sx[kStages];
+  uint8_t* sxlo[kStages];
+  uint8_t* sbh[kStages];
+  uint8_t* sbl[kStages];
+  for (int s = 0; s < kStages; ++s) {
+    sx[s] = smem + s * kStageBytes;
+    sxlo[s] = sx[s] + kXBytes;
+    sbh[s] = sxlo[s] + kXBytes;
+    sbl[s] = sbh[s] + kBBytes;
+  }
+  uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
+  uint64_t* full = bars;                 // TMA landed
+  uint64_t* conv = bars + kStages;       // hi/lo split done
+  uint64_t* empty = bars + 2 * kStages;  // MMAs of the stage done
+  uint64_t* accf = bars + 3 * kStages;   // accumulator complete
+  uint32_t* tmem_slot = (uint32_t*)(bars + 3 * kStages + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (pa.K + kChunkK - 1) / kChunkK;
+  // tile coordinates
+  long long row0 = 0;
+  int a0 = 0, bfix = 0;
+  if (pa.mode == 0) {
+    row0 = (long long)blockIdx.x * kTileM;
+  } else {
+    const int tiles_a = (pa.A + kTileM - 1) / kTileM;
+    bfix = blockIdx.x / tiles_a;
+    a0 = (blockIdx.x % tiles_a) * kTileM;
+  }
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 4);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kMaxN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const unsigned bytes = kXBytes + 2u * (unsigned)pa.Nout * kChunkK * 4u;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % kStages, it = c / kStages;
+        if (c >= kStages && !mbar_wait(&empty[s], (it - 1) & 1)) { atomicExch(&s_fail, 1); break; }
+        if (s_fail) break;
+        mbar_expect_tx(&full[s], bytes);
+        if (pa.mode == 0) tma_load_2d(sx[s], &tm_x, &full[s], c * kChunkK, (int)row0);
+        else tma_load_3d(sx[s], &tm_x, &full[s], c * kChunkK, bfix, a0);
+        tma_load_2d(sbh[s], &tm_bhi, &full[s], c * kChunkK, 0);
+        tma_load_2d(sbl[s], &tm_blo, &full[s], c * kChunkK, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(kTileM, pa.Nout);
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % kStages, it = c / kStages;
+        if (!mbar_wait(&conv[s], it & 1)) { atomicExch(&s_fail, 1); break; }
+        if (s_fail) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ax = smem_u32(sx[s]), al = smem_u32(sxlo[s]);
+        const uint32_t bh = smem_u32(sbh[s]), bl = smem_u32(sbl[s]);
+#pragma unroll
+        for (int kk = 0; kk < kChunkK / 8; ++kk) {
+          const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K inside the swizzle atom
+          const uint32_t accum = (c > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32(tmem, sw128_desc(ax + off), sw128_desc(bh + off), idesc, accum);
+          mma_tf32(tmem, sw128_desc(ax + off), sw128_desc(bl + off), idesc, 1u);
+          mma_tf32(tmem, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accf);
+    }
+  } else {
+    // warps 2-5: split X into hi/lo, then the epilogue
+    const int t = threadIdx.x - 64;   // 0..127
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % kStages, it = c / kStages;
+      // warp-uniform decision: every lane waits, the warp leaves together
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&full[s], it & 1));
+      if (!got) { atomicExch(&s_fail, 1); break; }
+      float4* px = reinterpret_cast<float4*>(sx[s]);
+      float4* pl = reinterpret_cast<float4*>(sxlo[s]);
+#pragma unroll 4
+      for (int e = t; e < kXBytes / 16; e += 128) {
+        float4 v = px[e];
+        float4 h, l;
+        h.x = tf32_rna(v.x); l.x = v.x - h.x;
+        h.y = tf32_rna(v.y); l.y = v.y - h.y;
+        h.z = tf32_rna(v.z); l.z = v.z - h.z;
+        h.w = tf32_rna(v.w); l.w = v.w - h.w;
+        px[e] = h;
+        pl[e] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+    bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0));
+    if (!ok) atomicExch(&s_fail, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = __all_sync(0xffffffffu, ok && (*(volatile int*)&s_fail == 0));   // tcgen05.ld needs a uniform warp
+    if (ok) {
+      const int wq = warp & 3;                 // TMEM lane quarter this warp may access
+      const int row = wq * 32 + lane;          // row within the tile
+      long long out_base;
+      long long col_stride;
+      bool valid;
+      if (pa.mode == 0) {
+        const long long r = row0 + row;
+        valid = r < pa.R;
+        out_base = r;
+        col_stride = pa.R;
+      } else {
+        const int a = a0 + row;
+        valid = a < pa.A;
+        out_base = (long long)bfix * pa.Kvalid * pa.A + a;
+        col_stride = pa.A;
+      }
+      for (int c0 = 0; c0 < pa.Nout; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (valid) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int k = c0 + j;
+            if (k < pa.Kvalid) pa.out[out_base + (long long)k * col_stride] = __uint_as_float(v[j]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMaxN));
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(pa.err, 1);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides_bytes,
+            const cuuint32_t* box) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void*)base, dims, strides_bytes, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_pass_supported(int K) { return K >= 4 && K <= kMaxN && K % 4 == 0; }
+
+int tc_smem_bytes() { return kSmemBytes; }
+
+// One pass: X viewed as [A][Bd][K] (ROWS_A) or [R][K] (ROWS_FLAT); Bhi/Blo are
+// [K][K] matrices (row k = output frequency).  Returns false if a tensor map
+// cannot be encoded (the caller reports DOT_ECUDA).
+bool launch_dct_pass_tc(const float* X, const float* Bhi, const float* Blo, float* out, int K, int mode,
+                        long long R, int A, int Bd, int* err, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dct_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    attr_set = true;
+  }
+  const int Nout = (K + 15) / 16 * 16;
+  CUtensorMap mx, mh, ml;
+  bool ok;
+  if (mode == 0) {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)R};
+    cuuint64_t str[1] = {(cuuint64_t)K * 4};
+    cuuint32_t box[2] = {kChunkK, kTileM};
+    ok = encode(&mx, X, 2, dims, str, box);
+  } else {
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)Bd, (cuuint64_t)A};
+    cuuint64_t str[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * 4 * Bd};
+    cuuint32_t box[3] = {kChunkK, 1, kTileM};
+    ok = encode(&mx, X, 3, dims, str, box);
+  }
+  cuuint64_t bdims[2] = {(cuuint64_t)K, (cuuint64_t)K};
+  cuuint64_t bstr[1] = {(cuuint64_t)K * 4};
+  cuuint32_t bbox[2] = {kChunkK, (cuuint32_t)Nout};
+  ok = ok && encode(&mh, Bhi, 2, bdims, bstr, bbox) && encode(&ml, Blo, 2, bdims, bstr, bbox);
+  if (!ok) return false;
+  PassArgs pa;
+  pa.out = out;
+  pa.K = K;
+  pa.Nout = Nout;
+  pa.Kvalid = K;
+  pa.mode = mode;
+  pa.R = R;
+  pa.A = A;
+  pa.Bd = Bd;
+  pa.err = err;
+  unsigned grid = mode == 0 ? (unsigned)((R + kTileM - 1) / kTileM)
+                            : (unsigned)(Bd * ((A + kTileM - 1) / kTileM));
+  k_dct_pass_tc<<<grid, kThreadsTC, kSmemBytes, s>>>(mx, mh, ml, pa);
+  return true;
+}
+
+}  // namespace dot

@@ -28,7 +28,7 @@ __global__ void k_assemble_b(Geo g, F64Fields f, double sigma) {
   const double isg = 1.0 / sigma;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     double acc = 0.0;
     if (t >= 1) acc += (f.q[0][i - g.P] - f.al[0][i - g.P] * isg) * g.invh[0];
@@ -85,7 +85,7 @@ __global__ void k_project(Geo g, F64Fields f, double sigma) {
   const double s_default = sqrt(0.5);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % g.P;
+    const long long p = i - (long long)plane_of(g, i) * g.P;
     double x[kMaxK];
     gather_Fq(g, f.q, i, p, x);
     const double s = f.somega ? f.somega[p] : s_default;
@@ -132,7 +132,7 @@ __global__ void k_update_qd(Geo g, F64Fields f, int d, double sigma, double tau)
   double* ad = f.al[1 + d];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     const int j = coord(g, p, d);
     if (j > g.N[d] - 2) continue;
@@ -186,7 +186,7 @@ __global__ void k_update_beta(Geo g, F64Fields f, double sigma, double tau) {
   const double ts = tau * sigma;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % g.P;
+    const long long p = i - (long long)plane_of(g, i) * g.P;
     double x[kMaxK];
     gather_Fq(g, f.q, i, p, x);
     const double s = f.somega ? f.somega[p] : s_default;
@@ -235,7 +235,7 @@ __global__ void k_kkt_cones(Geo g, F64Fields f, double* partials) {
   const int K = g.K;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % g.P;
+    const long long p = i - (long long)plane_of(g, i) * g.P;
     double x[kMaxK];
     gather_Fq(g, f.q, i, p, x);
     const double aphi = (f.phi[i + g.P] - f.phi[i]) * g.invh[0];
@@ -286,7 +286,7 @@ __global__ void k_kkt_faces(Geo g, F64Fields f, int d, double* partials) {
   const int cbase = 1 + 4 * d;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     const int j = coord(g, p, d);
     if (j > g.N[d] - 2) continue;
@@ -327,7 +327,7 @@ __global__ void k_kkt_nodes(Geo g, F64Fields f, double* partials) {
   const long long n = (long long)(g.T + 1) * g.P;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     double v = 0.0;
     if (t >= 1) v += f.al[0][i - g.P] * g.invh[0];

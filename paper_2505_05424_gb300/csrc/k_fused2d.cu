@@ -1,0 +1,364 @@
+// k_fused2d.cu -- lines 3-6 of Algorithm 2 (cone projection, q and alpha updates,
+// beta update) fused into one pass over the mixed-path state, for D = 2.
+//
+// A CTA owns a 16 x 32 (x, y) tile of the spatial grid and a chunk [ta, tb) of
+// cone times, and marches along time.  At cone time t it
+//   A. projects z(t) = Pi_K(B F q^k + d - beta^k/sigma) for the tile's cones and a
+//      one-cone halo ring, keeps u_v = z_v + beta_v/sigma (v = 1..8, the parts
+//      F^*B^* sends to space faces) in shared memory for two time levels, keeps the
+//      owned cones' z in registers, and updates q_0, alpha_0 of the owned cones
+//      (diagonal 3, Proposition 3.2);
+//   B. updates q_d, alpha_d at the faces of time node t that touch the tile
+//      (including the one halo face per axis that the tile's cones read);
+//   C. updates beta of the owned cones at time t-1, which needs q^{k+1} on the
+//      faces of time nodes t-1 and t (kept in shared memory).
+// beta is read once (plus an L2 re-read in C) and written once; z never reaches
+// HBM.  q, alpha and beta are double-buffered: every read is of iteration k and
+// every write of k+1, so neighbouring CTAs may run at any relative time.
+// The arithmetic per element is the same as k_mixed.cu's unfused kernels.
+#include <cmath>
+
+#include "dot_internal.cuh"
+#include "dot_mixed.cuh"
+#include "ffloat.cuh"
+
+namespace dot {
+namespace {
+
+constexpr int TX = 16, TY = 32;          // owned tile (x rows, y columns)
+constexpr int HX = TX + 2, HY = TY + 2;  // cone halo rectangle
+constexpr int NH = HX * HY;              // 612 cones
+constexpr int NRING = NH - TX * TY;      // 100 halo-ring cones
+constexpr int K2 = 10;                   // 4D + 2 for D = 2
+constexpr int kThreads = 256;
+constexpr int NQ1 = (TX + 1) * TY;       // x-faces per time node: j in [x0-1, x0+15], y owned
+constexpr int NQ2 = TX * (TY + 1);       // y-faces per time node: x owned, j in [y0-1, y0+31]
+
+struct FusedArgs {
+  // iteration k (read)
+  const float* q[3];
+  const float2* al[3];
+  const float2* beta;
+  // iteration k+1 (write)
+  float* qn[3];
+  float2* aln[3];
+  float2* betan;
+  const float2* phi;   // phi^{k+1}
+  const float* somega;
+  float2 isg;          // 1/sigma as a two-float
+  float ts;            // tau * sigma
+  int tchunk;
+  double* socp_part;   // per-block sum of |z - B F q^{k+1} - d|^2, or nullptr
+};
+
+// halo-ring cone number r (0..99) -> (xh, yh) on the border of the HX x HY rectangle
+__device__ __forceinline__ void ring_pos(int r, int* xh, int* yh) {
+  if (r < HY) { *xh = 0; *yh = r; return; }
+  r -= HY;
+  if (r < HY) { *xh = HX - 1; *yh = r; return; }
+  r -= HY;
+  if (r < HX - 2) { *xh = 1 + r; *yh = 0; return; }
+  r -= HX - 2;
+  *xh = 1 + r;
+  *yh = HY - 1;
+}
+
+__device__ __forceinline__ float2 grad_pair(const float2* phi, long long i, long long j, float invh) {
+  const float2 a = phi[i], b = phi[j];
+  const float2 dh = two_sum(b.x, -a.x);
+  const float dl = (b.y - a.y) + dh.y;
+  return make_float2(dh.x * invh, dl * invh);
+}
+
+__device__ __forceinline__ float grad_minus(float2 g, float q) { return (g.x - q) + g.y; }
+
+// z of cone (t, x, y) from iteration-k data, formed and projected in two-float
+// arithmetic (y = BFq + d - beta/sigma is dominated by beta/sigma); returns false
+// for a cone outside the grid.
+__device__ __forceinline__ bool cone_z(const Geo& g, const FusedArgs& a, int t, int x, int y, float2* z) {
+  if (x < 0 || y < 0 || x >= g.N[0] || y >= g.N[1]) return false;
+  const long long P = g.P, n0 = (long long)g.T * P;
+  const long long N1 = g.N[1];
+  const long long i = (long long)t * P + (long long)x * N1 + y;
+  const float* q1 = a.q[1];
+  const float* q2 = a.q[2];
+  const bool xl = x >= 1, xr = x <= g.N[0] - 2, yl = y >= 1, yr = y <= g.N[1] - 2;
+  float xv[K2 - 1];
+  xv[0] = a.q[0][i];
+  xv[1] = xl ? q1[i - N1] : 0.f;
+  xv[2] = xr ? q1[i] : 0.f;
+  xv[3] = xl ? q1[i + P - N1] : 0.f;
+  xv[4] = xr ? q1[i + P] : 0.f;
+  xv[5] = yl ? q2[i - 1] : 0.f;
+  xv[6] = yr ? q2[i] : 0.f;
+  xv[7] = yl ? q2[i + P - 1] : 0.f;
+  xv[8] = yr ? q2[i + P] : 0.f;
+  const float s = a.somega ? a.somega[(long long)x * N1 + y] : 0.70710678118654752f;
+  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(ff_mul(a.beta[i], a.isg)));
+#pragma unroll
+  for (int j = 1; j < K2 - 1; ++j)
+    z[j] = ff_add(two_prod(s, xv[j]), ff_neg(ff_mul(a.beta[(long long)j * n0 + i], a.isg)));
+  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(ff_mul(a.beta[(long long)(K2 - 1) * n0 + i], a.isg)));
+  ff_proj_soc<K2>(z);
+  return true;
+}
+
+constexpr int kSmemFused = (2 * 8 * NH) * 8 + (2 * NQ1 + 2 * NQ2) * 4;
+
+__global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a) {
+  // u_1..u_8 (two-float) of every halo cone at two time levels, then q^{k+1} on
+  // the tile's x-faces and y-faces at two node levels
+  extern __shared__ __align__(16) unsigned char fsm[];
+  float2 (*su)[8][NH] = reinterpret_cast<float2 (*)[8][NH]>(fsm);
+  float (*sq1)[NQ1] = reinterpret_cast<float (*)[NQ1]>(fsm + (2 * 8 * NH) * 8);
+  float (*sq2)[NQ2] = reinterpret_cast<float (*)[NQ2]>(fsm + (2 * 8 * NH) * 8 + 2 * NQ1 * 4);
+
+  const int tid = threadIdx.x;
+  const int ly = tid & 31, lx = tid >> 5;   // owned nodes (x0 + lx + 8r, y0 + ly)
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int ta = blockIdx.z * a.tchunk;
+  const int tb = min(g.T, ta + a.tchunk);
+  const bool last_chunk = (tb == g.T);
+  const long long P = g.P, n0 = (long long)g.T * P;
+  const long long N1 = g.N[1];
+  const float2 isg = a.isg;
+  const float ts = a.ts;
+  const float ih0 = (float)g.invh[0], ih1 = (float)g.invh[1], ih2 = (float)g.invh[2];
+  const float s_def = 0.70710678118654752f;
+
+  // registers of the two owned cones: z at the current and previous cone time,
+  // q_0^{k+1} at the previous cone time
+  float zc[2][K2], zp[2][K2];
+  float q0c[2] = {0.f, 0.f}, q0p[2] = {0.f, 0.f};
+  float socp = 0.f;
+  bool own_ok[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) own_ok[r] = (x0 + lx + 8 * r) < g.N[0] && (y0 + ly) < g.N[1];
+
+  const int tstart = ta > 0 ? ta - 1 : 0;
+  for (int t = tstart; t <= tb; ++t) {
+    const int lev = t & 1;
+    // ---------------- A: cones at time t ----------------
+    if (t <= g.T - 1) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int x = x0 + lx + 8 * r, y = y0 + ly;
+        const int hc = (lx + 8 * r + 1) * HY + (ly + 1);
+        float2 z[K2];
+        const bool ok = own_ok[r] && cone_z(g, a, t, x, y, z);
+        if (ok) {
+          const long long i = (long long)t * P + (long long)x * N1 + y;
+#pragma unroll
+          for (int v = 0; v < 8; ++v) su[lev][v][hc] = ff_add(z[1 + v], ff_mul(a.beta[(long long)(1 + v) * n0 + i], isg));
+          if (t >= ta && t < tb) {
+            // lines 4-5 on q_0: rhs = A_0 phi + (alpha_0 + beta_{K-1} - beta_0)/sigma + (z_{K-1} - z_0),
+            // diagonal 3, in two-float arithmetic
+            const float2 gp = grad_pair(a.phi, i, i + P, ih0);
+            const float2 al = a.al[0][i];
+            const float2 db = ff_add(a.beta[(long long)(K2 - 1) * n0 + i], ff_neg(a.beta[i]));
+            float2 rhs = ff_add(gp, ff_mul(ff_add(al, db), isg));
+            rhs = ff_add(rhs, ff_add(z[K2 - 1], ff_neg(z[0])));
+            const float qn = ff_round(ff_div_f(rhs, 3.f));
+            a.qn[0][i] = qn;
+            a.aln[0][i] = ff_add_f(al, ts * grad_minus(gp, qn));
+            q0c[r] = qn;   // becomes q0p at the end of this step
+          }
+#pragma unroll
+          for (int j = 0; j < K2; ++j) zc[r][j] = ff_round(z[j]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) su[lev][v][hc] = make_float2(0.f, 0.f);
+        }
+      }
+      for (int rr = tid; rr < NRING; rr += kThreads) {
+        int xh, yh;
+        ring_pos(rr, &xh, &yh);
+        const int x = x0 - 1 + xh, y = y0 - 1 + yh;
+        const int hc = xh * HY + yh;
+        float2 z[K2];
+        if (cone_z(g, a, t, x, y, z)) {
+          const long long i = (long long)t * P + (long long)x * N1 + y;
+#pragma unroll
+          for (int v = 0; v < 8; ++v) su[lev][v][hc] = ff_add(z[1 + v], ff_mul(a.beta[(long long)(1 + v) * n0 + i], isg));
+        } else {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) su[lev][v][hc] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- B: faces at time node t ----------------
+    if (t >= ta) {
+      const bool write_node = (t < tb) || (last_chunk && t == g.T);
+      const bool has_now = t <= g.T - 1, has_prev = t >= 1;
+      const int lp = lev ^ 1;
+      for (int e = tid; e < NQ1 + NQ2; e += kThreads) {
+        if (e < NQ1) {
+          // x-face (t, j, y): j = x0 - 1 + e / TY, y = y0 + e % TY
+          const int jx = e / TY, yy = e % TY;
+          const int j = x0 - 1 + jx, y = y0 + yy;
+          float qv = 0.f;
+          if (j >= 0 && j <= g.N[0] - 2 && y < g.N[1]) {
+            const long long i = (long long)t * P + (long long)j * N1 + y;
+            const float2 gp = grad_pair(a.phi, i, i + N1, ih1);
+            // cones (j+1, y) and (j, y) at halo rows jx+1 and jx, column yy+1
+            const int hr = (jx + 1) * HY + (yy + 1), hl = jx * HY + (yy + 1);
+            const float sr = a.somega ? a.somega[(long long)(j + 1) * N1 + y] : s_def;
+            const float sl = a.somega ? a.somega[(long long)j * N1 + y] : s_def;
+            float2 acc = make_float2(0.f, 0.f);
+            float dg = 0.f;
+            if (has_now) {
+              acc = ff_add(acc, ff_add(ff_mul_f(su[lev][0][hr], sr), ff_mul_f(su[lev][1][hl], sl)));
+              dg += sr * sr + sl * sl;
+            }
+            if (has_prev) {
+              acc = ff_add(acc, ff_add(ff_mul_f(su[lp][2][hr], sr), ff_mul_f(su[lp][3][hl], sl)));
+              dg += sr * sr + sl * sl;
+            }
+            const float2 al = a.al[1][i];
+            const float2 rhs = ff_add(ff_add(gp, ff_mul(al, isg)), acc);
+            qv = ff_round(ff_div_f(rhs, 1.f + dg));
+            if (write_node && jx >= 1) {
+              a.qn[1][i] = qv;
+              a.aln[1][i] = ff_add_f(al, ts * grad_minus(gp, qv));
+            }
+          }
+          sq1[lev][e] = qv;
+        } else {
+          // y-face (t, x, j): x = x0 + f / (TY+1), j = y0 - 1 + f % (TY+1)
+          const int f = e - NQ1;
+          const int xx = f / (TY + 1), jy = f % (TY + 1);
+          const int x = x0 + xx, j = y0 - 1 + jy;
+          float qv = 0.f;
+          if (x < g.N[0] && j >= 0 && j <= g.N[1] - 2) {
+            const long long i = (long long)t * P + (long long)x * N1 + j;
+            const float2 gp = grad_pair(a.phi, i, i + 1, ih2);
+            // cones (x, j+1) and (x, j) at halo row xx+1, columns jy+1 and jy
+            const int hr = (xx + 1) * HY + (jy + 1), hl = (xx + 1) * HY + jy;
+            const float sr = a.somega ? a.somega[(long long)x * N1 + j + 1] : s_def;
+            const float sl = a.somega ? a.somega[(long long)x * N1 + j] : s_def;
+            float2 acc = make_float2(0.f, 0.f);
+            float dg = 0.f;
+            if (has_now) {
+              acc = ff_add(acc, ff_add(ff_mul_f(su[lev][4][hr], sr), ff_mul_f(su[lev][5][hl], sl)));
+              dg += sr * sr + sl * sl;
+            }
+            if (has_prev) {
+              acc = ff_add(acc, ff_add(ff_mul_f(su[lp][6][hr], sr), ff_mul_f(su[lp][7][hl], sl)));
+              dg += sr * sr + sl * sl;
+            }
+            const float2 al = a.al[2][i];
+            const float2 rhs = ff_add(ff_add(gp, ff_mul(al, isg)), acc);
+            qv = ff_round(ff_div_f(rhs, 1.f + dg));
+            if (write_node && jy >= 1) {
+              a.qn[2][i] = qv;
+              a.aln[2][i] = ff_add_f(al, ts * grad_minus(gp, qv));
+            }
+          }
+          sq2[lev][f] = qv;
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- C: beta of the owned cones at time t-1 ----------------
+    if (t - 1 >= ta && t - 1 < tb) {
+      const int lp = lev ^ 1;   // node t-1 faces; node t faces at lev
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!own_ok[r]) continue;
+        const int xo = lx + 8 * r;   // 0..15
+        const int x = x0 + xo, y = y0 + ly;
+        const long long i = (long long)(t - 1) * P + (long long)x * N1 + y;
+        const bool xl = x >= 1, xr = x <= g.N[0] - 2, yl = y >= 1, yr = y <= g.N[1] - 2;
+        float xv[K2 - 1];
+        xv[0] = q0p[r];
+        // x-faces j = x-1 (row xo) and j = x (row xo+1) of the tile's face list
+        xv[1] = xl ? sq1[lp][xo * TY + ly] : 0.f;
+        xv[2] = xr ? sq1[lp][(xo + 1) * TY + ly] : 0.f;
+        xv[3] = xl ? sq1[lev][xo * TY + ly] : 0.f;
+        xv[4] = xr ? sq1[lev][(xo + 1) * TY + ly] : 0.f;
+        // y-faces j = y-1 (column ly) and j = y (column ly+1)
+        xv[5] = yl ? sq2[lp][xo * (TY + 1) + ly] : 0.f;
+        xv[6] = yr ? sq2[lp][xo * (TY + 1) + ly + 1] : 0.f;
+        xv[7] = yl ? sq2[lev][xo * (TY + 1) + ly] : 0.f;
+        xv[8] = yr ? sq2[lev][xo * (TY + 1) + ly + 1] : 0.f;
+        const float s = a.somega ? a.somega[(long long)x * N1 + y] : s_def;
+        const float* z = zp[r];
+        float inc = (z[0] - 1.f) + xv[0];
+        socp = fmaf(inc, inc, socp);
+        a.betan[i] = ff_add_f(a.beta[i], ts * inc);
+#pragma unroll
+        for (int j = 1; j < K2 - 1; ++j) {
+          const long long o = (long long)j * n0 + i;
+          inc = fmaf(-s, xv[j], z[j]);
+          socp = fmaf(inc, inc, socp);
+          a.betan[o] = ff_add_f(a.beta[o], ts * inc);
+        }
+        const long long o = (long long)(K2 - 1) * n0 + i;
+        inc = (z[K2 - 1] - 1.f) - xv[0];
+        socp = fmaf(inc, inc, socp);
+        a.betan[o] = ff_add_f(a.beta[o], ts * inc);
+      }
+    }
+    // the current cone time becomes the previous one
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      q0p[r] = q0c[r];
+#pragma unroll
+      for (int j = 0; j < K2; ++j) zp[r][j] = zc[r][j];
+    }
+    __syncthreads();
+  }
+  if (a.socp_part) {
+    // block sum of the beta increments' squares (the eta_P^soc term), FP64 tree
+    double v = (double)socp;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double wsum[kThreads / 32];
+    if ((tid & 31) == 0) wsum[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double b = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) b += wsum[w];
+      a.socp_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+    }
+  }
+}
+
+}  // namespace
+
+bool fused2d_supported(const Geo& g) { return g.D == 2; }
+
+long long fused2d_blocks(const Geo& g) {
+  const int tchunk = g.T <= 16 ? g.T : 16;
+  return (long long)((g.N[0] + TX - 1) / TX) * ((g.N[1] + TY - 1) / TY) * ((g.T + tchunk - 1) / tchunk);
+}
+
+void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
+                    double* socp_part, cudaStream_t s, LaunchCounter lc) {
+  FusedArgs a;
+  for (int d = 0; d < 3; ++d) {
+    a.q[d] = f.q[d];
+    a.al[d] = f.al[d];
+    a.qn[d] = fn.q[d];
+    a.aln[d] = fn.al[d];
+  }
+  a.beta = f.beta;
+  a.betan = fn.beta;
+  a.phi = f.phi;
+  a.somega = f.somega;
+  a.isg = ff_from_double(1.0 / (double)sigma);
+  a.ts = tau * sigma;
+  a.tchunk = g.T <= 16 ? g.T : 16;
+  a.socp_part = socp_part;
+  dim3 grid((unsigned)((g.N[0] + TX - 1) / TX), (unsigned)((g.N[1] + TY - 1) / TY),
+            (unsigned)((g.T + a.tchunk - 1) / a.tchunk));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fused2d, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFused);
+    attr = true;
+  }
+  k_fused2d<<<grid, kThreads, kSmemFused, s>>>(g, a);
+  lc.launched(KID_FUSED);
+}
+
+}  // namespace dot

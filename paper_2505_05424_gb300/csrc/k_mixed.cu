@@ -24,25 +24,37 @@ inline int grid_for(long long n) {
   return (int)b;
 }
 
-// A phi along an axis from the two-float potential: the difference of the hi
-// parts is exact or rounded relative to the difference itself.
-__device__ __forceinline__ float grad_ff(const float2* phi, long long i, long long j, float invh) {
+// A phi along an axis from the two-float potential, as an unevaluated pair
+// (gh, gl): gh + gl = (phi_j - phi_i) / h to ~2^-44 relative.
+__device__ __forceinline__ float2 grad_pair(const float2* phi, long long i, long long j, float invh) {
   const float2 a = phi[i], b = phi[j];
-  return ((b.x - a.x) + (b.y - a.y)) * invh;
+  const float2 dh = two_sum(b.x, -a.x);
+  const float dl = (b.y - a.y) + dh.y;
+  return make_float2(dh.x * invh, dl * invh);
 }
 
-// Line 1: b = A^*(q - alpha/sigma) - c/sigma.
+// A phi - q with one rounding relative to the (small) difference itself.
+__device__ __forceinline__ float grad_minus(float2 g, float q) { return (g.x - q) + g.y; }
+
+// Line 1: b = A^*(q - alpha/sigma) - c/sigma in two-float arithmetic (alpha/sigma
+// and c/sigma are 10-10^3 times the O(1) part that survives their cancellation).
 template <int D>
-__global__ void k_assemble_b(Geo g, MxFields f, float isg) {
+__global__ void k_assemble_b(Geo g, MxFields f, float2 isg) {
   const long long n = (long long)(g.T + 1) * g.P;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     const float ih0 = (float)g.invh[0];
-    float acc = 0.f;
-    if (t >= 1) acc += (f.q[0][i - g.P] - f.al[0][i - g.P].x * isg) * ih0;
-    if (t < g.T) acc -= (f.q[0][i] - f.al[0][i].x * isg) * ih0;
+    float2 acc = make_float2(0.f, 0.f);
+    if (t >= 1) {
+      const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i - g.P], isg)), f.q[0][i - g.P]);
+      acc = ff_add(acc, ff_mul_f(w, ih0));
+    }
+    if (t < g.T) {
+      const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i], isg)), f.q[0][i]);
+      acc = ff_add(acc, ff_neg(ff_mul_f(w, ih0)));
+    }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int x = coord(g, p, d);
@@ -50,25 +62,64 @@ __global__ void k_assemble_b(Geo g, MxFields f, float isg) {
       const float2* ad = f.al[1 + d];
       const long long s = g.sst[d];
       const float ih = (float)g.invh[1 + d];
-      if (x >= 1) acc += (qd[i - s] - ad[i - s].x * isg) * ih;
-      if (x <= g.N[d] - 2) acc -= (qd[i] - ad[i].x * isg) * ih;
+      if (x >= 1) {
+        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i - s], isg)), qd[i - s]);
+        acc = ff_add(acc, ff_mul_f(w, ih));
+      }
+      if (x <= g.N[d] - 2) {
+        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i], isg)), qd[i]);
+        acc = ff_add(acc, ff_neg(ff_mul_f(w, ih)));
+      }
     }
-    float c = 0.f;
-    if (t == 0) c += f.m0f[p];
-    if (t == g.T) c -= f.m1f[p];
-    f.b[i] = acc - c * isg;
+    if (t == 0) acc = ff_add(acc, ff_neg(ff_mul(f.c0[p], isg)));
+    if (t == g.T) acc = ff_add(acc, ff_mul(f.c1[p], isg));
+    f.b[i] = acc.x;
+    f.blo[i] = acc.y;
   }
 }
 
-// Refinement residual r = b - A^*A phi1, with A^*A phi1 accumulated exactly in
-// two-float arithmetic (each neighbour difference by TwoSum; 1/h^2 is an integer).
+// Sum of b in FP64 (per-block partials): the exact zero mode of the right-hand
+// side.  An FP32 DCT of a field with a large mean leaks O(u_32 * mean * sqrt(n))
+// into the other coefficients; removing the exact mean from the refinement
+// residual lets the correction solve remove that leak.
+constexpr int kMeanBlocks = 304;
+__global__ void k_sum_b(long long n, const float* __restrict__ b, const float* __restrict__ blo,
+                        double* partials) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc += (double)b[i] + (double)blo[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double w[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) s += w[k];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// Refinement residual r = b - mean(b) - A^*A phi1, with A^*A phi1 accumulated
+// exactly in two-float arithmetic (each neighbour difference by TwoSum; 1/h^2 is
+// an integer) and mean(b) from the FP64 partial sums.
 template <int D>
-__global__ void k_residual(Geo g, MxFields f) {
+__global__ void k_residual(Geo g, MxFields f, const double* bsum_partials) {
+  __shared__ float2 s_mean;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kMeanBlocks; ++k) s += bsum_partials[k];
+    const double m = s / (double)((long long)(g.T + 1) * g.P);
+    const float hi = (float)m;
+    s_mean = make_float2(hi, (float)(m - (double)hi));
+  }
+  __syncthreads();
+  const float2 mean = s_mean;
   const long long n = (long long)(g.T + 1) * g.P;
   const float* x = f.phi1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     const float xi = x[i];
     float2 acc = make_float2(0.f, 0.f);
@@ -89,7 +140,7 @@ __global__ void k_residual(Geo g, MxFields f) {
       const float ih = (float)g.invh[1 + d];
       acc = ff_add(acc, ff_mul_f(s, ih * ih));
     }
-    const float2 r = ff_add_f(ff_neg(acc), f.b[i]);
+    const float2 r = ff_add(make_float2(f.b[i], f.blo[i]), ff_neg(ff_add(acc, mean)));
     f.r[i] = r.x + r.y;
   }
 }
@@ -118,73 +169,59 @@ __device__ __forceinline__ void gather_Fq(const Geo& g, float* const* q, long lo
   }
 }
 
-template <int K>
-__device__ __forceinline__ void proj_soc(float* y) {
-  float nb2 = 0.f;
-#pragma unroll
-  for (int j = 1; j < K; ++j) nb2 = fmaf(y[j], y[j], nb2);
-  const float nb = sqrtf(nb2);
-  if (nb <= y[0]) return;
-  if (nb <= -y[0]) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) y[j] = 0.f;
-    return;
-  }
-  const float a = 0.5f * (y[0] + nb);
-  const float sc = a / nb;
-  y[0] = a;
-#pragma unroll
-  for (int j = 1; j < K; ++j) y[j] *= sc;
-}
-
-// Line 3: z = Pi_Q(B F q + d - beta/sigma).
+// Line 3: z = Pi_Q(B F q + d - beta/sigma), formed and projected in two-float
+// arithmetic (ff_proj_soc); z is stored rounded to FP32 (its O(1) value loses
+// only 2^-24 relative).
 template <int D>
-__global__ void k_project(Geo g, MxFields f, float isg) {
+__global__ void k_project(Geo g, MxFields f, float2 isg) {
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
   const float s_default = 0.70710678118654752f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % g.P;
+    const long long p = i - (long long)plane_of(g, i) * g.P;
     float x[K - 1];
     gather_Fq<D>(g, f.q, i, p, x);
     const float s = f.somega ? f.somega[p] : s_default;
-    float y[K];
-    y[0] = -x[0] + 1.f - f.beta[i].x * isg;
+    float2 y[K];
+    y[0] = ff_add(two_sum(-x[0], 1.f), ff_neg(ff_mul(f.beta[i], isg)));
 #pragma unroll
-    for (int j = 1; j < K - 1; ++j) y[j] = s * x[j] - f.beta[(long long)j * n0 + i].x * isg;
-    y[K - 1] = x[0] + 1.f - f.beta[(long long)(K - 1) * n0 + i].x * isg;
-    proj_soc<K>(y);
+    for (int j = 1; j < K - 1; ++j) y[j] = ff_add(two_prod(s, x[j]), ff_neg(ff_mul(f.beta[(long long)j * n0 + i], isg)));
+    y[K - 1] = ff_add(two_sum(x[0], 1.f), ff_neg(ff_mul(f.beta[(long long)(K - 1) * n0 + i], isg)));
+    ff_proj_soc<K>(y);
 #pragma unroll
-    for (int j = 0; j < K; ++j) f.z[(long long)j * n0 + i] = y[j];
+    for (int j = 0; j < K; ++j) f.z[(long long)j * n0 + i] = ff_round(y[j]);
   }
 }
 
-// Lines 4-5 on the time faces (diagonal 3, F^*B^*u = u_{K-1} - u_0).
+// Lines 4-5 on the time faces (diagonal 3, F^*B^*u = u_{K-1} - u_0), the
+// right-hand side in two-float arithmetic (alpha/sigma and beta/sigma cancel).
 template <int D>
-__global__ void k_update_q0(Geo g, MxFields f, float sigma, float tau) {
+__global__ void k_update_q0(Geo g, MxFields f, float2 isg, float ts) {
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
-  const float isg = 1.f / sigma, ts = tau * sigma;
   const float ih0 = (float)g.invh[0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const float aphi = grad_ff(f.phi, i, i + g.P, ih0);
-    const float uK = f.z[(long long)(K - 1) * n0 + i] + f.beta[(long long)(K - 1) * n0 + i].x * isg;
-    const float u0 = f.z[i] + f.beta[i].x * isg;
-    const float2 a = f.al[0][i];
-    const float qn = (aphi + a.x * isg + (uK - u0)) * (1.f / 3.f);
+    const float2 gp = grad_pair(f.phi, i, i + g.P, ih0);
+    const long long oK = (long long)(K - 1) * n0 + i;
+    // u_{K-1} - u_0 = (z_{K-1} - z_0) + (beta_{K-1} - beta_0)/sigma
+    const float2 db = ff_add(f.beta[oK], ff_neg(f.beta[i]));
+    float2 rhs = ff_add(gp, ff_mul(ff_add(f.al[0][i], db), isg));
+    rhs = ff_add_f(rhs, f.z[oK] - f.z[i]);
+    const float qn = ff_round(ff_div_f(rhs, 3.f));
     f.q[0][i] = qn;
-    f.al[0][i] = ff_add_f(a, ts * (aphi - qn));
+    f.al[0][i] = ff_add_f(f.al[0][i], ts * grad_minus(gp, qn));
   }
 }
 
-// Lines 4-5 on the faces of axis d (see the FP64 kernel for the cone bookkeeping).
+// Lines 4-5 on the faces of axis d (see the FP64 kernel for the cone bookkeeping):
+// rhs = A phi + (alpha + sum_c s_c beta_c)/sigma + sum_c s_c z_c with the
+// multiplier sum in two-float arithmetic.
 template <int D>
-__global__ void k_update_qd(Geo g, MxFields f, int d, float sigma, float tau) {
+__global__ void k_update_qd(Geo g, MxFields f, int d, float2 isg, float ts) {
   const long long n = (long long)(g.T + 1) * g.P;
   const long long n0 = (long long)g.T * g.P;
-  const float isg = 1.f / sigma, ts = tau * sigma;
   const float s_default = 0.70710678118654752f;
   const long long s = g.sst[d];
   float* qd = f.q[1 + d];
@@ -193,30 +230,33 @@ __global__ void k_update_qd(Geo g, MxFields f, int d, float sigma, float tau) {
   const int cbase = 1 + 4 * d;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     const int j = coord(g, p, d);
     if (j > g.N[d] - 2) continue;
-    const float aphi = grad_ff(f.phi, i, i + s, ih);
+    const float2 gp = grad_pair(f.phi, i, i + s, ih);
     const float s_r = f.somega ? f.somega[p + s] : s_default;
     const float s_l = f.somega ? f.somega[p] : s_default;
-    float acc = 0.f, dg = 0.f;
+    float2 mb = ad[i];          // alpha + sum s_c beta_c
+    float zs = 0.f, dg = 0.f;   // sum s_c z_c, sum s_c^2
     if (t <= g.T - 1) {
       const long long o1 = (long long)(cbase + 0) * n0 + i + s;
       const long long o2 = (long long)(cbase + 1) * n0 + i;
-      acc += s_r * (f.z[o1] + f.beta[o1].x * isg) + s_l * (f.z[o2] + f.beta[o2].x * isg);
+      mb = ff_add(mb, ff_add(ff_mul_f(f.beta[o1], s_r), ff_mul_f(f.beta[o2], s_l)));
+      zs += s_r * f.z[o1] + s_l * f.z[o2];
       dg += s_r * s_r + s_l * s_l;
     }
     if (t >= 1) {
       const long long o3 = (long long)(cbase + 2) * n0 + i - g.P + s;
       const long long o4 = (long long)(cbase + 3) * n0 + i - g.P;
-      acc += s_r * (f.z[o3] + f.beta[o3].x * isg) + s_l * (f.z[o4] + f.beta[o4].x * isg);
+      mb = ff_add(mb, ff_add(ff_mul_f(f.beta[o3], s_r), ff_mul_f(f.beta[o4], s_l)));
+      zs += s_r * f.z[o3] + s_l * f.z[o4];
       dg += s_r * s_r + s_l * s_l;
     }
-    const float2 a = ad[i];
-    const float qn = (aphi + a.x * isg + acc) / (1.f + dg);
+    const float2 rhs = ff_add_f(ff_add(gp, ff_mul(mb, isg)), zs);
+    const float qn = ff_round(ff_div_f(rhs, 1.f + dg));
     qd[i] = qn;
-    ad[i] = ff_add_f(a, ts * (aphi - qn));
+    ad[i] = ff_add_f(ad[i], ts * grad_minus(gp, qn));
   }
 }
 
@@ -228,18 +268,20 @@ __global__ void k_update_beta(Geo g, MxFields f, float ts) {
   const float s_default = 0.70710678118654752f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % g.P;
+    const long long p = i - (long long)plane_of(g, i) * g.P;
     float x[K - 1];
     gather_Fq<D>(g, f.q, i, p, x);
     const float s = f.somega ? f.somega[p] : s_default;
-    f.beta[i] = ff_add_f(f.beta[i], ts * (f.z[i] + x[0] - 1.f));
+    // increments z - BFq - d, each rounded once relative to itself:
+    // (z_0 - 1) and (z_{K-1} - 1) are exact for z in [1/2, 2]; z_j - s x_j by one FMA
+    f.beta[i] = ff_add_f(f.beta[i], ts * ((f.z[i] - 1.f) + x[0]));
 #pragma unroll
     for (int j = 1; j < K - 1; ++j) {
       const long long o = (long long)j * n0 + i;
-      f.beta[o] = ff_add_f(f.beta[o], ts * (f.z[o] - s * x[j]));
+      f.beta[o] = ff_add_f(f.beta[o], ts * fmaf(-s, x[j], f.z[o]));
     }
     const long long o = (long long)(K - 1) * n0 + i;
-    f.beta[o] = ff_add_f(f.beta[o], ts * (f.z[o] - x[0] - 1.f));
+    f.beta[o] = ff_add_f(f.beta[o], ts * ((f.z[o] - 1.f) - x[0]));
   }
 }
 
@@ -264,7 +306,7 @@ __device__ __forceinline__ void block_reduce_store(const float* accf, const doub
 }
 
 template <int D>
-__global__ void k_kkt_cones(Geo g, MxFields f, double* partials) {
+__global__ void k_kkt_cones(Geo g, MxFields f, double* partials, int use_z) {
   constexpr int K = 4 * D + 2;
   float acc[R_NSLOTS];
   double accd[R_NSLOTS];
@@ -274,12 +316,14 @@ __global__ void k_kkt_cones(Geo g, MxFields f, double* partials) {
   const float ih0 = (float)g.invh[0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i % g.P;
+    const long long p = i - (long long)plane_of(g, i) * g.P;
     float x[K - 1];
     gather_Fq<D>(g, f.q, i, p, x);
-    const float aphi = grad_ff(f.phi, i, i + g.P, ih0);
+    const float2 gp = grad_pair(f.phi, i, i + g.P, ih0);
+    const float aphi = gp.x + gp.y;
     const float q0 = x[0];
-    acc[R_PRIM] += (aphi - q0) * (aphi - q0);
+    const float dq = grad_minus(gp, q0);
+    acc[R_PRIM] += dq * dq;
     acc[R_APHI] += aphi * aphi;
     acc[R_Q] += q0 * q0;
     float ss = 0.f;
@@ -294,15 +338,17 @@ __global__ void k_kkt_cones(Geo g, MxFields f, double* partials) {
     acc[R_ALPHA0] += a0 * a0;
     acc[R_F] += fv * fv;
     const float s = f.somega ? f.somega[p] : s_default;
-    float r = f.z[i] + q0 - 1.f;
-    acc[R_SOCP] += r * r;
+    if (use_z) {
+      float r = (f.z[i] - 1.f) + q0;
+      acc[R_SOCP] += r * r;
 #pragma unroll
-    for (int j = 1; j < K - 1; ++j) {
-      r = f.z[(long long)j * n0 + i] - s * x[j];
+      for (int j = 1; j < K - 1; ++j) {
+        r = fmaf(-s, x[j], f.z[(long long)j * n0 + i]);
+        acc[R_SOCP] += r * r;
+      }
+      r = (f.z[(long long)(K - 1) * n0 + i] - 1.f) - q0;
       acc[R_SOCP] += r * r;
     }
-    r = f.z[(long long)(K - 1) * n0 + i] - q0 - 1.f;
-    acc[R_SOCP] += r * r;
     const float2 bK = f.beta[(long long)(K - 1) * n0 + i], b0 = f.beta[i];
     const float fbb = (bK.x - b0.x) + (bK.y - b0.y);
     acc[R_SOCD] += (fbb + a0) * (fbb + a0);
@@ -327,13 +373,15 @@ __global__ void k_kkt_faces(Geo g, MxFields f, int d, double* partials) {
   const float ih = (float)g.invh[1 + d];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     const int j = coord(g, p, d);
     if (j > g.N[d] - 2) continue;
-    const float aphi = grad_ff(f.phi, i, i + s, ih);
+    const float2 gp = grad_pair(f.phi, i, i + s, ih);
+    const float aphi = gp.x + gp.y;
     const float q = qd[i];
-    acc[R_PRIM] += (aphi - q) * (aphi - q);
+    const float dq = grad_minus(gp, q);
+    acc[R_PRIM] += dq * dq;
     acc[R_APHI] += aphi * aphi;
     acc[R_Q] += q * q;
     float den = 0.f, fbb = 0.f;
@@ -371,7 +419,7 @@ __global__ void k_kkt_nodes(Geo g, MxFields f, double* partials) {
   const long long n = (long long)(g.T + 1) * g.P;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(i / g.P);
+    const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
     float2 v = make_float2(0.f, 0.f);
     const float ih0 = (float)g.invh[0];
@@ -401,11 +449,13 @@ __global__ void k_kkt_nodes(Geo g, MxFields f, double* partials) {
   block_reduce_store(acc, accd, partials + (long long)blockIdx.x * R_NSLOTS);
 }
 
-__global__ void k_kkt_final(const double* partials, int rows, double* out) {
+__global__ void k_kkt_final(const double* partials, int rows, double* out, const double* socp_part, int nsocp) {
   __shared__ double sh[kThreads];
   for (int k = 0; k < R_NSLOTS; ++k) {
     double v = 0.0;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) v += partials[(long long)r * R_NSLOTS + k];
+    if (k == R_SOCP && socp_part)
+      for (int r = threadIdx.x; r < nsocp; r += blockDim.x) v += socp_part[r];
     sh[threadIdx.x] = v;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -424,8 +474,9 @@ void poisson_refined_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, 
                           LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P;
   launch_poisson_mx(g, ps, f.b, f.phi1, s, lc);
-  k_residual<D><<<grid_for(nn), kThreads, 0, s>>>(g, f);
-  lc.launched(KID_RESIDUAL);
+  k_sum_b<<<kMeanBlocks, kThreads, 0, s>>>(nn, f.b, f.blo, f.bsum);
+  k_residual<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, f.bsum);
+  lc.launched(KID_RESIDUAL, 2);
   launch_poisson_mx(g, ps, f.r, f.b, s, lc);
   k_combine<<<grid_for(nn), kThreads, 0, s>>>(nn, f.phi1, f.b, out);
   lc.launched(KID_COMBINE);
@@ -435,16 +486,17 @@ template <int D>
 void launch_iter_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, double sigma, double tau,
                       cudaStream_t s, LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
-  const float isg = (float)(1.0 / sigma);
+  const float2 isg = ff_from_double(1.0 / sigma);
+  const float ts = (float)(tau * sigma);
   k_assemble_b<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, isg);                 // line 1
   lc.launched(KID_ASSEMBLE_B);
   poisson_refined_tmpl<D>(g, f, ps, f.phi, s, lc);                                // line 2
   k_project<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, isg);                      // line 3
   lc.launched(KID_PROJECT);
-  k_update_q0<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, (float)sigma, (float)tau);  // lines 4-5
+  k_update_q0<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, isg, ts);                 // lines 4-5
   lc.launched(KID_UPDATE_Q0);
   for (int d = 0; d < D; ++d) {
-    k_update_qd<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, d, (float)sigma, (float)tau);
+    k_update_qd<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, d, isg, ts);
     lc.launched(KID_UPDATE_QD);
   }
   k_update_beta<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, (float)(tau * sigma));  // line 6
@@ -452,13 +504,13 @@ void launch_iter_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, doub
 }
 
 template <int D>
-void launch_kkt_tmpl(const Geo& g, const MxFields& f, double* partials, double* out, cudaStream_t s,
-                     LaunchCounter lc) {
-  k_kkt_cones<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, partials);
+void launch_kkt_tmpl(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
+                     int nsocp, cudaStream_t s, LaunchCounter lc) {
+  k_kkt_cones<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, partials, socp_part ? 0 : 1);
   for (int d = 0; d < D; ++d)
     k_kkt_faces<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, d, partials + (long long)(1 + d) * kKktBlocks * R_NSLOTS);
   k_kkt_nodes<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, partials + (long long)(1 + D) * kKktBlocks * R_NSLOTS);
-  k_kkt_final<<<1, kThreads, 0, s>>>(partials, (D + 2) * kKktBlocks, out);
+  k_kkt_final<<<1, kThreads, 0, s>>>(partials, (D + 2) * kKktBlocks, out, socp_part, nsocp);
   lc.launched(KID_KKT, D + 3);
 }
 
@@ -476,10 +528,18 @@ void launch_poisson_refined_mx(const Geo& g, const MxFields& f, const MxPoisson&
   else poisson_refined_tmpl<3>(g, f, ps, out, s, lc);
 }
 
-void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, cudaStream_t s,
-                   LaunchCounter lc) {
-  if (g.D == 2) launch_kkt_tmpl<2>(g, f, partials, out, s, lc);
-  else launch_kkt_tmpl<3>(g, f, partials, out, s, lc);
+void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
+                   int nsocp, cudaStream_t s, LaunchCounter lc) {
+  if (g.D == 2) launch_kkt_tmpl<2>(g, f, partials, out, socp_part, nsocp, s, lc);
+  else launch_kkt_tmpl<3>(g, f, partials, out, socp_part, nsocp, s, lc);
+}
+
+void launch_assemble_b_mx(const Geo& g, const MxFields& f, double sigma, cudaStream_t s, LaunchCounter lc) {
+  const long long nn = (long long)(g.T + 1) * g.P;
+  const float2 isg = ff_from_double(1.0 / sigma);
+  if (g.D == 2) k_assemble_b<2><<<grid_for(nn), kThreads, 0, s>>>(g, f, isg);
+  else k_assemble_b<3><<<grid_for(nn), kThreads, 0, s>>>(g, f, isg);
+  lc.launched(KID_ASSEMBLE_B);
 }
 
 long long kkt_partials_len_mx(const Geo& g) { return (long long)(g.D + 2) * kKktBlocks * R_NSLOTS; }

@@ -1,122 +1,253 @@
-// k_poisson_f32.cu -- FP32 Poisson solve of the mixed path: the orthonormal
-// DCT-II along every axis as a dense per-axis GEMM, division by the Neumann
-// eigenvalues (zero mode set to 0), DCT-III back (Sec. 4, phi-subproblem).
+// k_poisson_f32.cu -- the mixed-path Poisson solve A^*A phi = b on rge(A^*)
+// (Sec. 4, phi-subproblem of Algorithm 2): orthonormal DCT-II along every axis,
+// division by the Neumann eigenvalues with the zero mode set to 0, DCT-III back.
+//
+// Data flow ("rotated" passes): every spatial pass transforms the innermost axis
+// of its input and writes that axis outermost, so every pass is a K-major GEMM:
+//   2D  [t][x][y] -y-> [ky][t][x] -x-> [kx][ky][t] -t-solve-> [t][kx][ky]
+//       -ky^T-> [y][t][kx] -kx^T (rows along y)-> [t][x][y]
+//   3D  [t][x][y][z] -z-> -y-> -x-> [kx][ky][kz][t] -t-solve-> [t][kx][ky][kz]
+//       -kz^T-> -ky^T-> [y][z][t][kx] -kx^T (rows along (y,z))-> [t][x][y][z]
+// Spatial passes run on the tensor cores (k_dct_tc.cu, 3xTF32) when the axis
+// length allows a TMA tile, otherwise on the SIMT kernel below, which computes the
+// same pass in FP32 with the same output layout.  The time axis (length T+1) is
+// one fused pass per column of spatial frequencies: DCT-II, scale, DCT-III.
 #include "dot_mixed.cuh"
+#include "dot_tc.cuh"
 
 namespace dot {
 namespace {
 
 constexpr int kBM = 64, kBN = 64, kBK = 16, kPad = 68;
 
-// Y[o][k][i] = sum_m C[k][m] X[o][m][i] (or C^T); 256 threads, 4x4 outputs each.
-__global__ void __launch_bounds__(256) k_axis_f32(const float* __restrict__ C, const float* __restrict__ X,
-                                                  float* __restrict__ Y, int M, long long inner, long long ncol,
-                                                  int transpose) {
-  __shared__ __align__(16) float As[kBK][kPad];  // As[m][k]
-  __shared__ __align__(16) float Bs[kBK][kPad];  // Bs[m][col]
+// SIMT rotated pass.  Rows r of the input are contiguous K-vectors.
+// mode 0: row r -> Out[k*R + r];  mode 1: row (a, b) -> Out[b*K*A + k*A + a].
+__global__ void __launch_bounds__(256) k_rot_pass_f32(const float* __restrict__ Bm, const float* __restrict__ X,
+                                                      float* __restrict__ Y, int K, long long R, int mode, int A,
+                                                      int Bd, FastDiv fA) {
+  __shared__ __align__(16) float Ws[kBK][kPad];   // Ws[j][k] = Bm[k][j]
+  __shared__ __align__(16) float Xs[kBK][kPad];   // Xs[j][row]
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const long long col0 = (long long)blockIdx.x * kBN;
+  const long long row0 = (long long)blockIdx.x * kBN;
   const int k0 = blockIdx.y * kBM;
   float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int m0 = 0; m0 < M; m0 += kBK) {
+  for (int j0 = 0; j0 < K; j0 += kBK) {
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int e = tid + 256 * jj;
       const int r = e / kBK, c = e % kBK;
-      const int k = k0 + r, m = m0 + c;
-      float v = 0.f;
-      if (k < M && m < M) v = transpose ? C[(long long)m * M + k] : C[(long long)k * M + m];
-      As[c][r] = v;
+      const int k = k0 + r, j = j0 + c;
+      Ws[c][r] = (k < K && j < K) ? Bm[(long long)k * K + j] : 0.f;
     }
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int e = tid + 256 * jj;
-      int r, c;
-      if (inner == 1) { c = e / kBK; r = e % kBK; } else { r = e / kBN; c = e % kBN; }
-      const int m = m0 + r;
-      const long long col = col0 + c;
-      float v = 0.f;
-      if (m < M && col < ncol) {
-        const long long o = col / inner, i = col - o * inner;
-        v = X[(o * M + m) * inner + i];
+      const int c = e / kBK, r = e % kBK;     // consecutive threads read consecutive j
+      const long long row = row0 + c;
+      const int j = j0 + r;
+      long long src = -1;
+      if (row < R && j < K) {
+        if (mode == 0) {
+          src = row * K + j;
+        } else {
+          // row enumerates (b, a) with a fastest: a = row % A, b = row / A
+          const long long b = fdiv((unsigned)row, fA), a = row - b * A;
+          src = (a * Bd + b) * K + j;
+        }
       }
-      Bs[r][c] = v;
+      Xs[r][c] = src >= 0 ? X[src] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      const float4 w = *reinterpret_cast<const float4*>(&Ws[kk][ty * 4]);
+      const float4 x = *reinterpret_cast<const float4*>(&Xs[kk][tx * 4]);
+      const float wv[4] = {w.x, w.y, w.z, w.w}, xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wv[a], xv[b], acc[a][b]);
     }
     __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int k = k0 + ty * 4 + a;
-    if (k >= M) continue;
+    if (k >= K) continue;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const long long col = col0 + tx * 4 + b;
-      if (col >= ncol) continue;
-      const long long o = col / inner, i = col - o * inner;
-      Y[(o * M + k) * inner + i] = acc[a][b];
+      const long long row = row0 + tx * 4 + b;
+      if (row >= R) continue;
+      long long dst;
+      if (mode == 0) {
+        dst = (long long)k * R + row;
+      } else {
+        const long long bb = fdiv((unsigned)row, fA), aa = row - bb * A;
+        dst = bb * (long long)K * A + (long long)k * A + aa;
+      }
+      Y[dst] = acc[a][b];
     }
   }
 }
 
-__global__ void k_scale_lambda_f32(Geo g, MxPoisson ps, float* v) {
-  const long long n = (long long)(g.T + 1) * g.P;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (i == 0) { v[0] = 0.f; continue; }
-    const int kt = (int)(i / g.P);
-    const long long p = i - (long long)kt * g.P;
-    float lam = ps.lam[0][kt];
-    for (int d = 0; d < g.D; ++d) lam += ps.lam[1 + d][coord(g, p, d)];
-    v[i] = v[i] / lam;
+// Time axis: X = [S][M] (M = T+1 innermost) -> Y = [M][S]:
+//   Y[:, s] = C_t^T diag(1/lambda(., s)) C_t X[s, :]   (lambda(0, 0) -> zero mode).
+// 64 columns s per block.  C_t (zero-padded to Mp = 16*ceil(M/16)), the tile and
+// its transform live in shared memory; thread (tk, ts) owns rows tk + 16i and the
+// four columns 4ts..4ts+3, so each shared load feeds several FMAs.
+constexpr int kTsRowsMax = 10;   // Mp <= 160
+__global__ void __launch_bounds__(256) k_tsolve_f32(Geo g, const float* __restrict__ Ct,
+                                                    const float* __restrict__ lam_t, MxPoisson ps,
+                                                    const float* __restrict__ X, float* __restrict__ Y) {
+  extern __shared__ __align__(16) float sm[];
+  const int M = g.T + 1;
+  const int Mp = (M + 15) / 16 * 16;
+  const int R = Mp / 16;
+  const long long S = g.P;
+  float* C = sm;                 // Mp*Mp, C[k*Mp + t]
+  float* xt = C + Mp * Mp;       // Mp*64: xt[t][s]
+  float* yt = xt + Mp * 64;      // Mp*64
+  const long long s0 = (long long)blockIdx.x * 64;
+  for (int e = threadIdx.x; e < Mp * Mp; e += blockDim.x) {
+    const int k = e / Mp, t = e % Mp;
+    C[e] = (k < M && t < M) ? Ct[k * M + t] : 0.f;
+  }
+  for (int e = threadIdx.x; e < Mp * 64; e += blockDim.x) {
+    const int s = e / Mp, t = e % Mp;   // consecutive threads read consecutive t of one column
+    const long long col = s0 + s;
+    xt[t * 64 + s] = (col < S && t < M) ? X[col * M + t] : 0.f;
+  }
+  __syncthreads();
+  const int tk = threadIdx.x >> 4, ts = threadIdx.x & 15;
+  float acc[kTsRowsMax][4];
+  // forward DCT-II along t
+#pragma unroll
+  for (int i = 0; i < kTsRowsMax; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int t = 0; t < Mp; ++t) {
+    const float4 b = *reinterpret_cast<const float4*>(&xt[t * 64 + 4 * ts]);
+#pragma unroll
+    for (int i = 0; i < kTsRowsMax; ++i) {
+      if (i < R) {
+        const float a = C[(tk + 16 * i) * Mp + t];
+        acc[i][0] = fmaf(a, b.x, acc[i][0]);
+        acc[i][1] = fmaf(a, b.y, acc[i][1]);
+        acc[i][2] = fmaf(a, b.z, acc[i][2]);
+        acc[i][3] = fmaf(a, b.w, acc[i][3]);
+      }
+    }
+  }
+  // scale by 1/lambda(k, s); the zero mode (k = 0, s = 0) is set to 0
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long col = s0 + 4 * ts + j;
+    float lsp = 0.f;
+    for (int d = 0; d < g.D; ++d) lsp += ps.lam[1 + d][coord(g, col < S ? col : 0, d)];
+#pragma unroll
+    for (int i = 0; i < kTsRowsMax; ++i) {
+      if (i < R) {
+        const int k = tk + 16 * i;
+        const float lam = (k < M ? lam_t[k] : 1.f) + lsp;
+        yt[k * 64 + 4 * ts + j] = (k == 0 && col == 0) ? 0.f : acc[i][j] / lam;
+      }
+    }
+  }
+  __syncthreads();
+  // inverse DCT-III along t: out[t][s] = sum_k C[k][t] yt[k][s]
+#pragma unroll
+  for (int i = 0; i < kTsRowsMax; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k = 0; k < Mp; ++k) {
+    const float4 b = *reinterpret_cast<const float4*>(&yt[k * 64 + 4 * ts]);
+#pragma unroll
+    for (int i = 0; i < kTsRowsMax; ++i) {
+      if (i < R) {
+        const float a = C[k * Mp + tk + 16 * i];
+        acc[i][0] = fmaf(a, b.x, acc[i][0]);
+        acc[i][1] = fmaf(a, b.y, acc[i][1]);
+        acc[i][2] = fmaf(a, b.z, acc[i][2]);
+        acc[i][3] = fmaf(a, b.w, acc[i][3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kTsRowsMax; ++i) {
+    const int t = tk + 16 * i;
+    if (i >= R || t >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long col = s0 + 4 * ts + j;
+      if (col < S) Y[(long long)t * S + col] = acc[i][j];
+    }
   }
 }
 
-void axis(const Geo& g, int a, const float* C, int transpose, const float* X, float* Y, cudaStream_t s,
-          LaunchCounter lc) {
-  const long long nn = (long long)(g.T + 1) * g.P;
-  const int M = a == 0 ? g.T + 1 : g.N[a - 1];
-  const long long inner = a == 0 ? g.P : g.sst[a - 1];
-  const long long ncol = nn / M;
-  dim3 grid((unsigned)((ncol + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM));
-  k_axis_f32<<<grid, 256, 0, s>>>(C, X, Y, M, inner, ncol, transpose);
+// One spatial pass of length K over total elements n: tensor cores when possible.
+void spatial_pass(const MxPoisson& ps, int axis, bool inverse, const float* X, float* Y, int K, long long n,
+                  int mode, int A, int Bd, cudaStream_t s, LaunchCounter lc) {
+  const long long R = n / K;
+  const float* Bhi = inverse ? ps.CThi[axis] : ps.Chi[axis];
+  const float* Blo = inverse ? ps.CTlo[axis] : ps.Clo[axis];
+  if (ps.use_tc && tc_pass_supported(K) &&
+      launch_dct_pass_tc(X, Bhi, Blo, Y, K, mode, R, A, Bd, ps.err, s)) {
+    lc.launched(KID_DCT_TC);
+    return;
+  }
+  const float* Bm = inverse ? ps.CT[axis] : ps.C[axis];
+  dim3 grid((unsigned)((R + kBN - 1) / kBN), (unsigned)((K + kBM - 1) / kBM));
+  k_rot_pass_f32<<<grid, 256, 0, s>>>(Bm, X, Y, K, R, mode, A, Bd, make_fastdiv((unsigned)(A > 0 ? A : 1)));
   lc.launched(KID_DCT_AXIS);
 }
 
 }  // namespace
 
+size_t tsolve_smem_bytes(const Geo& g) {
+  const size_t Mp = ((size_t)g.T + 1 + 15) / 16 * 16;
+  return (Mp * Mp + 2 * Mp * 64) * sizeof(float);
+}
+
 void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
                        LaunchCounter lc) {
+  const long long n = (long long)(g.T + 1) * g.P;
   float* w[2] = {ps.w1, ps.w2};
-  int ci = 0;
-  axis(g, 0, ps.C[0], 0, src, w[0], s, lc);
-  for (int a = 1; a <= g.D; ++a) {
-    axis(g, a, ps.C[a], 0, w[ci], w[1 - ci], s, lc);
-    ci = 1 - ci;
+  int ci = -1;   // index of the buffer holding the current field, -1 = src
+  auto cur = [&]() -> const float* { return ci < 0 ? src : w[ci]; };
+  auto next = [&]() { return ci < 0 ? 0 : 1 - ci; };
+  // forward spatial passes, innermost axis first
+  for (int a = g.D; a >= 1; --a) {
+    const int nx = next();
+    spatial_pass(ps, a, false, cur(), w[nx], g.N[a - 1], n, 0, 0, 0, s, lc);
+    ci = nx;
   }
-  const long long nn = (long long)(g.T + 1) * g.P;
-  long long blocks = (nn + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_scale_lambda_f32<<<(int)blocks, 256, 0, s>>>(g, ps, w[ci]);
-  lc.launched(KID_SCALE);
-  for (int a = 0; a <= g.D; ++a) {
-    float* out = (a == g.D) ? dst : w[1 - ci];
-    axis(g, a, ps.C[a], 1, w[ci], out, s, lc);
-    ci = 1 - ci;
+  {
+    const int nx = next();
+    const size_t sm = tsolve_smem_bytes(g);
+    static size_t attr = 0;
+    if (sm > 48 * 1024 && sm > attr) {
+      cudaFuncSetAttribute(k_tsolve_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = sm;
+    }
+    k_tsolve_f32<<<(unsigned)((g.P + 63) / 64), 256, sm, s>>>(g, ps.C[0], ps.lam[0], ps, cur(), w[nx]);
+    lc.launched(KID_SCALE);
+    ci = nx;
+  }
+  // inverse spatial passes, innermost axis first; the last one (axis 1) runs with
+  // rows along the flattened trailing spatial axes so it lands in [t][x][...]
+  for (int a = g.D; a >= 1; --a) {
+    const bool last = (a == 1);
+    float* out = last ? dst : w[next()];
+    const int K = g.N[a - 1];
+    const int mode = last ? 1 : 0;
+    const int A = last ? (int)(g.P / K) : 0;
+    const int Bd = last ? g.T + 1 : 0;
+    spatial_pass(ps, a, true, cur(), out, K, n, mode, A, Bd, s, lc);
+    if (!last) ci = next();
   }
 }
 

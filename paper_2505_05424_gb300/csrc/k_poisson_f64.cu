@@ -26,7 +26,7 @@ __device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b)
 // 32x32 sub-tile (rows 32*(w>>1), cols 32*(w&1)) as 4x4 fragments of 8x8.
 __global__ void __launch_bounds__(128) k_axis_dmma(const double* __restrict__ C, const double* __restrict__ X,
                                                    double* __restrict__ Y, int M, long long inner,
-                                                   long long ncol, int transpose) {
+                                                   long long ncol, int transpose, FastDiv finner) {
   __shared__ double As[kBM][kAPad];
   __shared__ double Bs[kBK][kBPad];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(128) k_axis_dmma(const double* __restrict__ C,
       const long long col = col0 + c;
       double v = 0.0;
       if (m < M && col < ncol) {
-        const long long o = col / inner, i = col - o * inner;
+        const long long o = fdiv((unsigned)col, finner), i = col - o * inner;
         v = X[(o * M + m) * inner + i];
       }
       Bs[r][c] = v;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(128) k_axis_dmma(const double* __restrict__ C,
       for (int h = 0; h < 2; ++h) {
         const long long col = col0 + cbase + 8 * b + 2 * (lane & 3) + h;
         if (col >= ncol) continue;
-        const long long o = col / inner, i = col - o * inner;
+        const long long o = fdiv((unsigned)col, finner), i = col - o * inner;
         Y[(o * M + k) * inner + i] = acc[a][b][h];
       }
     }
@@ -104,7 +104,7 @@ __global__ void k_scale_lambda(Geo g, DctTables64 t, double* v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     if (i == 0) { v[0] = 0.0; continue; }
-    const int kt = (int)(i / g.P);
+    const int kt = plane_of(g, i);
     const long long p = i - (long long)kt * g.P;
     double lam = t.lam[0][kt];
     for (int d = 0; d < g.D; ++d) lam += t.lam[1 + d][coord(g, p, d)];
@@ -119,7 +119,7 @@ void axis_transform(const Geo& g, int axis, const double* C, int transpose, cons
   long long inner = axis == 0 ? g.P : g.sst[axis - 1];
   long long ncol = n_nodes / M;
   dim3 grid((unsigned)((ncol + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM));
-  k_axis_dmma<<<grid, 128, 0, s>>>(C, X, Y, M, inner, ncol, transpose);
+  k_axis_dmma<<<grid, 128, 0, s>>>(C, X, Y, M, inner, ncol, transpose, make_fastdiv((unsigned)inner));
   lc.launched(KID_DCT_AXIS);
 }
 

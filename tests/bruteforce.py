@@ -34,9 +34,11 @@ class DenseDOT:
         self.ncone = self.A[0].shape[0]
 
     def c(self, m0, m1):
+        """eq. (defc) with the data as cell-average densities (mass / cell area)."""
+        area = float(np.prod([1.0 / n for n in self.N]))
         c = np.zeros(self.node_shape)
-        c[0] = np.asarray(m0).reshape(self.N)
-        c[-1] = -np.asarray(m1).reshape(self.N)
+        c[0] = np.asarray(m0).reshape(self.N) / area
+        c[-1] = -np.asarray(m1).reshape(self.N) / area
         return c.ravel()
 
     def f(self, phi, omega):

@@ -31,3 +31,20 @@ def random_state(g, rng, scale=1.0):
     al = rng.standard_normal(g.n_q) * scale * 0.1
     beta = rng.standard_normal(g.K * g.n_cones) * scale
     return q, al, beta
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_solution(name, tol=1e-6, maxit=60000):
+    """Oracle solve of a named workload from zero (cached for the test session)."""
+    key = (name, tol)
+    if key not in _ORACLE_CACHE:
+        from paper_2505_05424_gb300 import workloads as W
+        spec, r0, r1, mask = W.workload(name)
+        g = O.Grid(spec.D, spec.T, [spec.N] * spec.D)
+        prob = O.Problem(g, r0, r1, mask)
+        st = O.State.zeros(g)
+        res = O.solve(prob, st, tol=tol, maxit=maxit)
+        _ORACLE_CACHE[key] = (spec, r0, r1, mask, g, prob, st, res)
+    return _ORACLE_CACHE[key]

@@ -25,12 +25,24 @@ def _lib():
     ensure_built()
 
 
+# odd sizes (SIMT DCT passes), and axis lengths divisible by 4 (tensor-core DCT
+# passes) with row counts that leave ragged 128-row tiles, up to a 256-long axis
 GRIDS = [(2, 4, [6, 5]), (2, 1, [2, 2]), (2, 69, [70, 3]), (2, 7, [9, 131]), (3, 3, [4, 3, 5]),
-         (3, 5, [6, 7, 66])]
+         (3, 5, [6, 7, 66]), (2, 5, [32, 36]), (2, 9, [256, 64]), (2, 16, [32, 32]), (3, 3, [8, 12, 16]),
+         (2, 64, [128, 128])]
 
 
 def f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def centred(v):
+    """phi modulo constants.  The FP32 DCT rows are orthogonal to the constant vector
+    only up to rounding and A^*A cannot see constants, so the mixed solve leaves an
+    O(u_32 |phi|) constant in phi; A removes it and sum(c) = 0, so q, alpha, beta and
+    the objective do not depend on it."""
+    v = np.asarray(v, dtype=np.float64).ravel()
+    return v - v.mean()
 
 
 @pytest.mark.parametrize("D,T,N", GRIDS)
@@ -42,7 +54,7 @@ def test_refined_poisson(D, T, N):
     _, _, gpu = pair(D, T, N, r0, r0, prec="mixed")
     phi = gpu.dot_poisson(b)
     ref = O.poisson(g, b)
-    assert rel_err(phi, ref) < 1e-9
+    assert rel_err(centred(phi), ref) < 1e-9
     gpu.close()
 
 
@@ -64,33 +76,36 @@ def test_one_iteration_from_random_state(D, T, N, masked):
     q2, al2, b2, _, it = gpu.dot_get_state()
     _, _, phi, _, _ = gpu.dot_get()
     assert it == 1
-    assert rel_err(phi.ravel(), st.phi) < STEP_TOL
+    assert rel_err(centred(phi), st.phi) < STEP_TOL
     assert rel_err(q2, st.q) < STEP_TOL
     assert rel_err(al2, st.alpha) < STEP_TOL
     assert rel_err(b2, st.beta) < STEP_TOL
     kg, ko = gpu.dot_kkt(), O.kkt(prob, st)
     for name in ("eta_P", "eta_D", "eta_C", "eta_P_soc", "eta_D_soc"):
-        assert abs(kg[name] - ko[name]) <= 1e-3 * abs(ko[name]) + 1e-7, name
+        assert abs(kg[name] - ko[name]) <= 1e-3 * abs(ko[name]) + 1e-6, name
     assert abs(kg["primal_obj"] - ko["primal_obj"]) <= STEP_TOL * max(abs(ko["primal_obj"]), 1e-12)
     gpu.close()
 
 
 def test_gauss32_mixed_converges_to_fp64_objective():
-    """2D 32^2 x 16 two Gaussians + floor: mixed reaches KKT 1e-6 and matches the
-    FP64 oracle's objective (continued to eta <= 1e-7) and densities."""
-    spec, r0, r1, mask = W.workload("gauss32")
-    g, prob, gpu = pair(2, spec.T, [spec.N] * 2, r0, r1, prec="mixed")
-    st = O.State.zeros(g)
-    res = O.solve(prob, st, tol=1e-7, maxit=60000)
-    rc = gpu.dot_solve(tol=1e-6, maxit=20000)
+    """2D 32^2 x 16 two Gaussians + floor: mixed reaches KKT 1e-6 and its objective is
+    within 1e-6 relative of the FP64 oracle's at the same tolerance."""
+    from gpu_util import oracle_solution
+    spec, r0, r1, mask, g, prob, st, res = oracle_solution("gauss32")
+    gpu = pair(2, spec.T, [spec.N] * 2, r0, r1, prec="mixed")[2]
+    rc = gpu.dot_solve(tol=1e-6, maxit=40000)
     assert rc == 0
     rho, m, phi, obj, kk = gpu.dot_get()
     assert kk["eta_dot"] <= 1e-6
-    ref = -2 * res["primal_obj"]
-    print("mixed iters", kk["iterations"], "obj", obj, "ref", ref, "rel", abs(obj - ref) / abs(ref),
-          "max|rho-rho_o|", np.abs(rho - O.density_slices(g, st)).max())
-    assert abs(obj - ref) <= 1e-5 * abs(ref)
-    assert np.abs(rho - O.density_slices(g, st)).max() <= 1e-3 * np.abs(rho).max()
+    ref = O.w2_squared(g, res["primal_obj"])
+    rho_o = O.density_slices(g, st)
+    print("mixed iters", kk["iterations"], "oracle iters", res["iterations"], "obj", obj, "ref", ref,
+          "rel", abs(obj - ref) / abs(ref), "max|rho-rho_o|/max", np.abs(rho - rho_o).max() / rho_o.max())
+    assert abs(obj - ref) <= 1e-6 * abs(ref)
+    # both iterates stop at eta_dot <= 1e-6; at that tolerance the densities of two
+    # runs agree to ~0.5% of their maximum on this grid (FP64 at 1e-6 vs 1e-7 differ
+    # by as much), so this is a sanity bound, not a precision claim
+    assert np.abs(rho - rho_o).max() <= 1e-2 * rho_o.max()
     gpu.close()
 
 

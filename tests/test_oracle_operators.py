@@ -145,12 +145,13 @@ def test_cone_membership_equals_P(D, T, N, weighted):
         assert np.all((in_cone[sel] >= 0) == (f[sel] <= 0))
 
 
-def test_c_vector_masses():
-    """eq. (defc): rho_0 masses on the first time slice, minus rho_1 masses on the last."""
+def test_c_vector_densities():
+    """eq. (defc): rho_0 on the first time slice, minus rho_1 on the last, as cell-average
+    densities (mass / cell area); zero in between."""
     g = O.Grid(2, 3, [4, 5])
     rng = np.random.default_rng(5)
     m0, m1 = rng.random(20), rng.random(20)
     c = O.fill_c(g, m0, m1).reshape(g.node_shape)
-    np.testing.assert_array_equal(c[0].ravel(), m0)
-    np.testing.assert_array_equal(c[-1].ravel(), -m1)
+    np.testing.assert_allclose(c[0].ravel(), m0 * 20, rtol=1e-15)
+    np.testing.assert_allclose(c[-1].ravel(), -m1 * 20, rtol=1e-15)
     assert np.all(c[1:-1] == 0)
