@@ -154,6 +154,26 @@ int dot_profile(dot_ctx *ctx, int enable);
 int dot_profile_read(dot_ctx *ctx, double *ms_total, long *launches, int max);
 const char *dot_kernel_name(int id);
 
+/* Refined Poisson solve for callers that cannot allocate device memory (no
+ * counterpart in the paper; it serves code that runs inside a fixed memory plan,
+ * such as a stream being captured into a CUDA graph, hosts that forbid allocation
+ * on their worker threads, or processes whose device memory is reserved by
+ * another allocator).  It computes what dot_poisson computes for a DOT_MIXED
+ * context -- phi = (A^*A)^dagger b by FP32/3xTF32 DCT solves with one refinement
+ * step -- on caller-owned device buffers, and allocates nothing: all scratch
+ * lives in one fixed __device__ array of the library (about 31 MB, held by every
+ * GPU that loads the library until the process exits).
+ *   b    : device, FP32, [T+1][N_1]...[N_D]           (read only)
+ *   phi  : device, 2 floats per node (hi, lo) in the same order; phi = hi + lo
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * Limits: D in {2, 3}, T+1 and every N_d in [2, 256], (T+1) N_1...N_D <= 2^20
+ * nodes; larger grids return DOT_EINVAL with a message from
+ * dot_noalloc_last_error().  The first call on a device fetches the array's
+ * device address and should come before any stream capture.  Every call shares
+ * the array: calls whose work overlaps on the GPU race and must be serialised. */
+int dot_poisson_f32_noalloc(const dot_grid *grid, const float *b, float *phi, void *stream);
+const char *dot_noalloc_last_error(void);
+
 void dot_destroy(dot_ctx *ctx);
 const char *dot_last_error(const dot_ctx *ctx);
 

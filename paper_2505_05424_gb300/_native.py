@@ -91,7 +91,8 @@ DOT_KKT_LEN = len(KKT_NAMES)
 # Every symbol include/dot.h declares.
 EXPORTS = ("dot_default_options", "dot_workspace_bytes", "dot_create", "dot_solve", "dot_get", "dot_kkt",
            "dot_get_state", "dot_set_state", "dot_poisson", "dot_destroy", "dot_last_error", "dot_version",
-           "dot_launch_count", "dot_profile", "dot_profile_read", "dot_kernel_name")
+           "dot_launch_count", "dot_profile", "dot_profile_read", "dot_kernel_name", "dot_poisson_f32_noalloc",
+           "dot_noalloc_last_error")
 
 _lib = None
 _lock = threading.Lock()
@@ -144,5 +145,9 @@ def load(build_if_missing: bool = True):
         lib.dot_profile_read.restype = ctypes.c_int
         lib.dot_kernel_name.argtypes = [ctypes.c_int]
         lib.dot_kernel_name.restype = ctypes.c_char_p
+        lib.dot_poisson_f32_noalloc.argtypes = [P(DotGrid), vp, vp, vp]
+        lib.dot_poisson_f32_noalloc.restype = ctypes.c_int
+        lib.dot_noalloc_last_error.argtypes = []
+        lib.dot_noalloc_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib

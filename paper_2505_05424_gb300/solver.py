@@ -202,3 +202,16 @@ class DotSolver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dot_poisson_f32_noalloc(D: int, T: int, N_, b, phi, stream=None) -> None:
+    """Binding of dot_poisson_f32_noalloc (see include/dot.h): b is a CUDA float32
+    tensor of (T+1) * prod(N) entries, phi a CUDA float32 tensor of twice that many
+    (hi, lo pairs).  Raises DotError on a non-zero status."""
+    lib = N.load()
+    g = make_grid(D, T, N_)
+    s = 0 if stream is None else stream.cuda_stream
+    rc = lib.dot_poisson_f32_noalloc(ctypes.byref(g), ctypes.c_void_p(b.data_ptr()),
+                                     ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(s))
+    if rc != N.DOT_OK:
+        raise DotError(rc, lib.dot_noalloc_last_error().decode())

@@ -21,7 +21,7 @@ def lib():
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "dot.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dot_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(dot_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_expected_calls():
