@@ -36,7 +36,7 @@ WORKLOAD_DESC = ("2D DOT 256x256 cells x 64 time steps, seeded mixtures of 1-5 G
 # eta_dot <= 1e-6 on the seed-1002 instance of this workload; converts the oracle's
 # seconds per iteration into solves/s in the reference arm.  Measured by this script's
 # own arm ("fp64" -> "iterations" in its JSON line).
-ORACLE_ITERS_PER_SOLVE = None
+ORACLE_ITERS_PER_SOLVE = 11120
 
 
 def parse():
@@ -52,7 +52,26 @@ def parse():
     ap.add_argument("--fp64-maxit", type=int, default=40000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64"])
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="run this many iterations of one solve (no stopping checks) and exit: a short, "
+                         "fixed launch sequence for ncu; prints no JSON")
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """A fixed launch sequence for profilers: one context, N iterations, no checks."""
+    import torch
+    from paper_2505_05424_gb300 import workloads as W
+    from paper_2505_05424_gb300 import _native
+    _native.build()
+    spec, r0, r1, m = W.workload(args.workload)
+    s = make_solver(spec, r0, r1, m, args.prec, check_every=0)
+    s.dot_solve(0.0, args.profile_iters)
+    torch.cuda.synchronize()
+    print(f"profile case: {args.workload} {args.prec} {args.profile_iters} iterations, "
+          f"{s.launch_count()} launches", file=sys.stderr)
+    s.close()
 
 
 def load_peaks():
@@ -139,8 +158,15 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
         "poisson_residual": 3 * 4 * nc,
         "poisson_combine": (4 + 4 + 8) * nc,
         "dct_scale": 2 * (8 if prec == "fp64" else 4) * nc,
+        # lines 3-6 fused: read q, alpha, beta (iteration k) and phi; write q, alpha, beta (k+1)
+        "fused_cone_update": 2 * (w + ws) * nq + 2 * ws * K * n0 + wf * nc,
     }
     return float(table.get(name, 0.0))
+
+
+# DRAM bytes (read + write) of one launch, from an ncu capture of the mix256 workload
+# (profiles/k_fused2d_tma_mix256.md); valid while the kernel is unchanged since.
+NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"): 594.088448e6 + 451.743232e6}
 
 
 def make_solver(spec, r0, r1, mask, prec, **kw):
@@ -250,8 +276,9 @@ def run_ours(args):
     else:
         achieved = abytes / (per_launch_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
+        traffic = NCU_TRAFFIC.get((dname, WORKLOAD, args.prec))
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None, "kernel": dname,
+                "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": dname,
                 "per_launch_ms": round(per_launch_ms, 5), "algorithmic_bytes": abytes,
                 "peak_source": f"{peak_src} (of measured copy bandwidth)" if peak_src == "measured" else peak_src}
 
@@ -378,6 +405,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.profile_iters > 0:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -14,7 +14,7 @@ struct MxFields {
   float* blo;              // (T+1)*P right-hand side, low part (b = b + blo as a two-float)
   float* phi1;             // (T+1)*P first Poisson solve
   float* r;                // (T+1)*P refinement residual
-  double* bsum;            // 304 FP64 partial sums of b (zero mode of the right-hand side)
+  double* bsum;            // kBsumParts FP64 partial sums of b, then mean(b) as a two-float
   const float2* c0;        // P: c on the first time plane (densities, two-float)
   const float2* c1;        // P: -c on the last time plane (rho1 densities, two-float)
   const double* m0;        // P: rho0 densities (FP64, for the reductions)
@@ -45,9 +45,11 @@ size_t tsolve_smem_bytes(const Geo& g);
 // src -> dst (src is preserved), FP32 in and out.
 void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
                        LaunchCounter lc);
-// Refined solve of f.b into out (two-float); f.b is overwritten.
+// Refined solve of f.b (+ f.blo) into out (two-float); f.b is overwritten.
+// have_bsum: f.bsum already holds the partial sums of b (k_assemble_b writes them).
+constexpr int kBsumParts = 608;
 void launch_poisson_refined_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out,
-                               cudaStream_t s, LaunchCounter lc);
+                               bool have_bsum, cudaStream_t s, LaunchCounter lc);
 void launch_iterate_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, double sigma, double tau,
                        cudaStream_t s, LaunchCounter lc);
 // Stopping-measure sums.  socp_part (nullable): per-block sums of |z - BFq - d|^2
@@ -62,6 +64,12 @@ bool fused2d_supported(const Geo& g);
 long long fused2d_blocks(const Geo& g);
 void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
                     double* socp_part, cudaStream_t s, LaunchCounter lc);
+// The same pass with beta staged by TMA (needs N_y even); socp_part:
+// fused2d_tma_blocks(g) doubles.  Returns false if the tensor map cannot be built.
+bool fused2d_tma_supported(const Geo& g);
+long long fused2d_tma_blocks(const Geo& g);
+bool launch_fused2d_tma(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
+                        double* socp_part, int* err, cudaStream_t s, LaunchCounter lc);
 long long kkt_partials_len_mx(const Geo& g);
 
 }  // namespace dot

@@ -45,7 +45,7 @@ constexpr size_t kOffW2 = kOffW1 + kField;
 constexpr size_t kOffTables = kOffW2 + kField;                           // (kMaxD+1) axes x 6 tables
 constexpr size_t kOffLam = kOffTables + (size_t)(kMaxD + 1) * 6 * kTable; // (kMaxD+1) axes
 constexpr size_t kOffSum = kOffLam + (size_t)(kMaxD + 1) * kLam;
-constexpr size_t kOffErr = kOffSum + 512 * sizeof(double);   // the zero-mode reduction writes 304
+constexpr size_t kOffErr = kOffSum + 1024 * sizeof(double);  // kBsumParts partial sums, then mean(b)
 constexpr size_t kScratchBytes = kOffErr + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -177,7 +177,8 @@ extern "C" int dot_poisson_f32_noalloc(const dot_grid* grid, const float* b, flo
   if (e != cudaSuccess) return fail(DOT_ECUDA, "scratch set-up: ", cudaGetErrorString(e));
   long launches = 0;
   LaunchCounter lc{&launches};
-  launch_poisson_refined_mx(g, f, ps, reinterpret_cast<float2*>(phi), s, lc);
+  static_assert(kBsumParts + 2 <= 1024, "scratch holds 1024 doubles of partial sums and mean");
+  launch_poisson_refined_mx(g, f, ps, reinterpret_cast<float2*>(phi), false, s, lc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DOT_ECUDA, "launch: ", cudaGetErrorString(e));
   int flag = 0;

@@ -335,6 +335,16 @@ bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t* dims,
 
 }  // namespace
 
+bool encode_tensor_map(CUtensorMap* m, CUtensorMapDataType type, int rank, const void* base,
+                       const cuuint64_t* dims, const cuuint64_t* strides_bytes, const cuuint32_t* box) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(m, type, rank, (void*)base, dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool tc_pass_supported(int K) { return K >= 4 && K <= kMaxN && K % 4 == 0; }
 
 int tc_smem_bytes() { return kSmemBytes; }

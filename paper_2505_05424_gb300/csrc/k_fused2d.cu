@@ -20,6 +20,7 @@
 
 #include "dot_internal.cuh"
 #include "dot_mixed.cuh"
+#include "dot_tc.cuh"
 #include "ffloat.cuh"
 
 namespace dot {
@@ -49,6 +50,7 @@ struct FusedArgs {
   float ts;            // tau * sigma
   int tchunk;
   double* socp_part;   // per-block sum of |z - B F q^{k+1} - d|^2, or nullptr
+  int* err;            // set when a pipeline wait gave up
 };
 
 // halo-ring cone number r (0..99) -> (xh, yh) on the border of the HX x HY rectangle
@@ -350,6 +352,7 @@ void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double 
   a.ts = tau * sigma;
   a.tchunk = g.T <= 16 ? g.T : 16;
   a.socp_part = socp_part;
+  a.err = nullptr;
   dim3 grid((unsigned)((g.N[0] + TX - 1) / TX), (unsigned)((g.N[1] + TY - 1) / TY),
             (unsigned)((g.T + a.tchunk - 1) / a.tchunk));
   static bool attr = false;
@@ -359,6 +362,381 @@ void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double 
   }
   k_fused2d<<<grid, kThreads, kSmemFused, s>>>(g, a);
   lc.launched(KID_FUSED);
+}
+
+}  // namespace dot
+
+// ---------------------------------------------------------------------------
+// v2: the same pass with beta staged through shared memory by TMA.
+//
+// beta is three quarters of the pass's traffic.  One elected thread loads each
+// time step's beta tile -- all 10 components of a 10 x 36 (x, y) window around
+// the CTA's 8 x 32 tile -- with one 4-D TMA box into a ring of three buffers, so
+// the load for cone time t+1 runs while the CTA computes time t (buffer t-1 is
+// still needed by the faces and the beta update).  q, alpha and phi are small and
+// read directly.  Requires N_y even (TMA: 16-byte row strides and an even start
+// column for 8-byte elements).
+namespace dot {
+namespace {
+
+constexpr int VX = 8, VY = 32;               // owned tile: one cone per thread
+constexpr int VHX = VX + 2, VHY = VY + 2;    // cone halo 10 x 34
+constexpr int VNH = VHX * VHY;               // 340 cones
+constexpr int VBW = VY + 4;                  // beta tile columns: y in [y0-2, y0+34)
+constexpr int VNQ1 = (VX + 1) * VY;          // 288 x-faces: j in [x0-1, x0+7], y owned
+constexpr int VNQ2 = VX * (VY + 1);          // 264 y-faces: x owned, j in [y0-1, y0+31]
+constexpr int kBetaTile = K2 * VHX * VBW;    // 3600 two-floats = 28800 bytes
+constexpr int kBetaTileBytes = kBetaTile * 8;
+constexpr int kOffZ = 3 * kBetaTileBytes;                 // z tile: [2][8][VNH] floats
+constexpr int kOffQ1 = kOffZ + 2 * 8 * VNH * 4;          // [2][VNQ1] floats
+constexpr int kOffQ2 = kOffQ1 + 2 * VNQ1 * 4;            // [2][VNQ2] floats
+constexpr int kOffBar = (kOffQ2 + 2 * VNQ2 * 4 + 15) / 16 * 16;
+constexpr int kSmemV2 = kOffBar + 64;
+constexpr unsigned kSpinV2 = 1u << 25;
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = sa(bar);
+  for (unsigned it = 0; it < kSpinV2; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void issue_beta(const CUtensorMap* tm, float2* dst, uint64_t* bar, int y, int x, int t) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(kBetaTileBytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];"
+      ::"r"(sa(dst)), "l"(tm), "r"(sa(bar)), "r"(y), "r"(x), "r"(t), "r"(0)
+      : "memory");
+}
+
+// beta of halo cone (xh, yh) component c in a tile (column yw = yh + 1)
+__device__ __forceinline__ float2 bt(const float2* tile, int c, int xh, int yh) {
+  return tile[(c * VHX + xh) * VBW + yh + 1];
+}
+
+// z of cone (t, x, y) from the iteration-k q (global) and a beta tile, in two-float
+// arithmetic as cone_z; false for a cone outside the grid.
+__device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, const float2* tile, int t, int x,
+                                            int y, int xh, int yh, float2* z) {
+  if (x < 0 || y < 0 || x >= g.N[0] || y >= g.N[1]) return false;
+  const int P = (int)g.P, N1 = g.N[1];
+  const int i = t * P + x * N1 + y;
+  const float* q1 = a.q[1];
+  const float* q2 = a.q[2];
+  const bool xl = x >= 1, xr = x <= g.N[0] - 2, yl = y >= 1, yr = y <= g.N[1] - 2;
+  float xv[K2 - 1];
+  xv[0] = a.q[0][i];
+  xv[1] = xl ? q1[i - N1] : 0.f;
+  xv[2] = xr ? q1[i] : 0.f;
+  xv[3] = xl ? q1[i + P - N1] : 0.f;
+  xv[4] = xr ? q1[i + P] : 0.f;
+  xv[5] = yl ? q2[i - 1] : 0.f;
+  xv[6] = yr ? q2[i] : 0.f;
+  xv[7] = yl ? q2[i + P - 1] : 0.f;
+  xv[8] = yr ? q2[i + P] : 0.f;
+  const float s = a.somega ? a.somega[x * N1 + y] : 0.70710678118654752f;
+  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(ff_mul(bt(tile, 0, xh, yh), a.isg)));
+#pragma unroll
+  for (int j = 1; j < K2 - 1; ++j) z[j] = ff_add(two_prod(s, xv[j]), ff_neg(ff_mul(bt(tile, j, xh, yh), a.isg)));
+  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(ff_mul(bt(tile, K2 - 1, xh, yh), a.isg)));
+  ff_proj_soc<K2>(z);
+  return true;
+}
+
+__global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ CUtensorMap tmb, Geo g,
+                                                        FusedArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  float2* btiles = reinterpret_cast<float2*>(sm);
+  float (*zt)[8][VNH] = reinterpret_cast<float (*)[8][VNH]>(sm + kOffZ);
+  float (*sq1)[VNQ1] = reinterpret_cast<float (*)[VNQ1]>(sm + kOffQ1);
+  float (*sq2)[VNQ2] = reinterpret_cast<float (*)[VNQ2]>(sm + kOffQ2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
+
+  const int tid = threadIdx.x;
+  const int ly = tid & 31, lx = tid >> 5;       // owned node (x0 + lx, y0 + ly)
+  const int x0 = blockIdx.x * VX, y0 = blockIdx.y * VY;
+  const int ta = blockIdx.z * a.tchunk;
+  const int tb = min(g.T, ta + a.tchunk);
+  const bool last_chunk = (tb == g.T);
+  const int P = (int)g.P, n0 = g.T * P, N1 = g.N[1];
+  const float2 isg = a.isg;
+  const float ts = a.ts;
+  const float ih0 = (float)g.invh[0], ih1 = (float)g.invh[1], ih2 = (float)g.invh[2];
+  const float s_def = 0.70710678118654752f;
+  const int xo = x0 + lx, yo = y0 + ly;
+  const bool own_ok = xo < g.N[0] && yo < g.N[1];
+  const int tstart = ta > 0 ? ta - 1 : 0;
+  const int tlast_cone = min(tb, g.T - 1);      // last cone time whose beta tile is loaded
+
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bars[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phase[3] = {0u, 0u, 0u};
+  bool inflight[3] = {false, false, false};   // meaningful on the issuing thread
+  if (tid == 0 && tstart <= tlast_cone) {
+    issue_beta(&tmb, btiles + (tstart % 3) * kBetaTile, &bars[tstart % 3], y0 - 2, x0 - 1, tstart);
+    inflight[tstart % 3] = true;
+  }
+
+  float zc[K2], zp[K2];
+  float q0c = 0.f, q0p = 0.f, socp = 0.f;
+  bool failed = false;
+
+  for (int t = tstart; t <= tb; ++t) {
+    const int lev = t & 1, lp = lev ^ 1;
+    const int bcur = t % 3, bprev = (t + 2) % 3;
+    const float2* tcur = btiles + bcur * kBetaTile;
+    const float2* tprev = btiles + bprev * kBetaTile;
+    // prefetch the next cone time's beta into the buffer freed at the end of step t-1
+    if (tid == 0 && t + 1 <= tlast_cone) {
+      const int nb = (t + 1) % 3;
+      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1);
+      inflight[nb] = true;
+    }
+    if (t <= g.T - 1) {
+      const bool ok = bar_wait(&bars[bcur], phase[bcur]);
+      if (ok) {
+        phase[bcur] ^= 1u;
+        inflight[bcur] = false;
+      }
+      if (__syncthreads_or(!ok)) { failed = true; break; }
+    }
+    // ---------------- A: cones at time t ----------------
+    if (t <= g.T - 1) {
+      {
+        const int xh = lx + 1, yh = ly + 1, hc = xh * VHY + yh;
+        float2 z[K2];
+        if (own_ok && cone_z_tile(g, a, tcur, t, xo, yo, xh, yh, z)) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = ff_round(z[1 + v]);
+          if (t >= ta && t < tb) {
+            const int i = t * P + xo * N1 + yo;
+            const float2 gp = grad_pair(a.phi, i, i + P, ih0);
+            const float2 al = a.al[0][i];
+            const float2 db = ff_add(bt(tcur, K2 - 1, xh, yh), ff_neg(bt(tcur, 0, xh, yh)));
+            float2 rhs = ff_add(gp, ff_mul(ff_add(al, db), isg));
+            rhs = ff_add(rhs, ff_add(z[K2 - 1], ff_neg(z[0])));
+            const float qn = ff_round(ff_div_f(rhs, 3.f));
+            a.qn[0][i] = qn;
+            a.aln[0][i] = ff_add_f(al, ts * grad_minus(gp, qn));
+            q0c = qn;
+          }
+#pragma unroll
+          for (int j = 0; j < K2; ++j) zc[j] = ff_round(z[j]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = 0.f;
+        }
+      }
+      // the 84 halo-ring cones
+      if (tid < VNH - VX * VY) {
+        int r = tid, xh, yh;
+        if (r < VHY) { xh = 0; yh = r; }
+        else if ((r -= VHY) < VHY) { xh = VHX - 1; yh = r; }
+        else if ((r -= VHY) < VHX - 2) { xh = 1 + r; yh = 0; }
+        else { r -= VHX - 2; xh = 1 + r; yh = VHY - 1; }
+        const int hc = xh * VHY + yh;
+        float2 z[K2];
+        if (cone_z_tile(g, a, tcur, t, x0 - 1 + xh, y0 - 1 + yh, xh, yh, z)) {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = ff_round(z[1 + v]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- B: faces at time node t ----------------
+    if (t >= ta) {
+      const bool write_node = (t < tb) || (last_chunk && t == g.T);
+      const bool has_now = t <= g.T - 1, has_prev = t >= 1;
+      for (int e = tid; e < VNQ1 + VNQ2; e += 256) {
+        if (e < VNQ1) {
+          const int jx = e / VY, yy = e % VY;
+          const int j = x0 - 1 + jx, y = y0 + yy;
+          float qv = 0.f;
+          if (j >= 0 && j <= g.N[0] - 2 && y < g.N[1]) {
+            const int i = t * P + j * N1 + y;
+            const float2 gp = grad_pair(a.phi, i, i + N1, ih1);
+            const int xr = jx + 1, xl = jx, yh = yy + 1;
+            const float sr = a.somega ? a.somega[(j + 1) * N1 + y] : s_def;
+            const float sl = a.somega ? a.somega[j * N1 + y] : s_def;
+            float2 mb = a.al[1][i];
+            float zs = 0.f, dg = 0.f;
+            if (has_now) {
+              mb = ff_add(mb, ff_add(ff_mul_f(bt(tcur, 1, xr, yh), sr), ff_mul_f(bt(tcur, 2, xl, yh), sl)));
+              zs += sr * zt[lev][0][xr * VHY + yh] + sl * zt[lev][1][xl * VHY + yh];
+              dg += sr * sr + sl * sl;
+            }
+            if (has_prev) {
+              mb = ff_add(mb, ff_add(ff_mul_f(bt(tprev, 3, xr, yh), sr), ff_mul_f(bt(tprev, 4, xl, yh), sl)));
+              zs += sr * zt[lp][2][xr * VHY + yh] + sl * zt[lp][3][xl * VHY + yh];
+              dg += sr * sr + sl * sl;
+            }
+            const float2 rhs = ff_add_f(ff_add(gp, ff_mul(mb, isg)), zs);
+            qv = ff_round(ff_div_f(rhs, 1.f + dg));
+            if (write_node && jx >= 1) {
+              a.qn[1][i] = qv;
+              a.aln[1][i] = ff_add_f(a.al[1][i], ts * grad_minus(gp, qv));
+            }
+          }
+          sq1[lev][e] = qv;
+        } else {
+          const int f = e - VNQ1;
+          const int xx = f / (VY + 1), jy = f % (VY + 1);
+          const int x = x0 + xx, j = y0 - 1 + jy;
+          float qv = 0.f;
+          if (x < g.N[0] && j >= 0 && j <= g.N[1] - 2) {
+            const int i = t * P + x * N1 + j;
+            const float2 gp = grad_pair(a.phi, i, i + 1, ih2);
+            const int xh = xx + 1, yr = jy + 1, yl = jy;
+            const float sr = a.somega ? a.somega[x * N1 + j + 1] : s_def;
+            const float sl = a.somega ? a.somega[x * N1 + j] : s_def;
+            float2 mb = a.al[2][i];
+            float zs = 0.f, dg = 0.f;
+            if (has_now) {
+              mb = ff_add(mb, ff_add(ff_mul_f(bt(tcur, 5, xh, yr), sr), ff_mul_f(bt(tcur, 6, xh, yl), sl)));
+              zs += sr * zt[lev][4][xh * VHY + yr] + sl * zt[lev][5][xh * VHY + yl];
+              dg += sr * sr + sl * sl;
+            }
+            if (has_prev) {
+              mb = ff_add(mb, ff_add(ff_mul_f(bt(tprev, 7, xh, yr), sr), ff_mul_f(bt(tprev, 8, xh, yl), sl)));
+              zs += sr * zt[lp][6][xh * VHY + yr] + sl * zt[lp][7][xh * VHY + yl];
+              dg += sr * sr + sl * sl;
+            }
+            const float2 rhs = ff_add_f(ff_add(gp, ff_mul(mb, isg)), zs);
+            qv = ff_round(ff_div_f(rhs, 1.f + dg));
+            if (write_node && jy >= 1) {
+              a.qn[2][i] = qv;
+              a.aln[2][i] = ff_add_f(a.al[2][i], ts * grad_minus(gp, qv));
+            }
+          }
+          sq2[lev][f] = qv;
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- C: beta of the owned cone at time t-1 ----------------
+    if (own_ok && t - 1 >= ta && t - 1 < tb) {
+      const int i = (t - 1) * P + xo * N1 + yo;
+      const bool xl = xo >= 1, xr = xo <= g.N[0] - 2, yl = yo >= 1, yr = yo <= g.N[1] - 2;
+      float xv[K2 - 1];
+      xv[0] = q0p;
+      xv[1] = xl ? sq1[lp][lx * VY + ly] : 0.f;
+      xv[2] = xr ? sq1[lp][(lx + 1) * VY + ly] : 0.f;
+      xv[3] = xl ? sq1[lev][lx * VY + ly] : 0.f;
+      xv[4] = xr ? sq1[lev][(lx + 1) * VY + ly] : 0.f;
+      xv[5] = yl ? sq2[lp][lx * (VY + 1) + ly] : 0.f;
+      xv[6] = yr ? sq2[lp][lx * (VY + 1) + ly + 1] : 0.f;
+      xv[7] = yl ? sq2[lev][lx * (VY + 1) + ly] : 0.f;
+      xv[8] = yr ? sq2[lev][lx * (VY + 1) + ly + 1] : 0.f;
+      const float s = a.somega ? a.somega[xo * N1 + yo] : s_def;
+      const int xh = lx + 1, yh = ly + 1;
+      float inc = (zp[0] - 1.f) + xv[0];
+      socp = fmaf(inc, inc, socp);
+      a.betan[i] = ff_add_f(bt(tprev, 0, xh, yh), ts * inc);
+#pragma unroll
+      for (int j = 1; j < K2 - 1; ++j) {
+        inc = fmaf(-s, xv[j], zp[j]);
+        socp = fmaf(inc, inc, socp);
+        a.betan[j * n0 + i] = ff_add_f(bt(tprev, j, xh, yh), ts * inc);
+      }
+      inc = (zp[K2 - 1] - 1.f) - xv[0];
+      socp = fmaf(inc, inc, socp);
+      a.betan[(K2 - 1) * n0 + i] = ff_add_f(bt(tprev, K2 - 1, xh, yh), ts * inc);
+    }
+    q0p = q0c;
+#pragma unroll
+    for (int j = 0; j < K2; ++j) zp[j] = zc[j];
+    __syncthreads();
+  }
+  if (failed) {
+    // a tile load did not complete in time: wait (bounded) for the loads this
+    // CTA still has in flight, then report through the error flag
+    if (tid == 0) {
+      for (int b = 0; b < 3; ++b)
+        if (inflight[b]) bar_wait(&bars[b], phase[b]);
+      atomicExch(a.err, 1);
+    }
+    return;
+  }
+  if (a.socp_part) {
+    double v = (double)socp;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double wsum[8];
+    if ((tid & 31) == 0) wsum[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double b = 0.0;
+      for (int w = 0; w < 8; ++w) b += wsum[w];
+      a.socp_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace dot
+
+namespace dot {
+
+bool fused2d_tma_supported(const Geo& g) { return g.D == 2 && g.N[1] % 2 == 0; }
+
+long long fused2d_tma_blocks(const Geo& g) {
+  const int tchunk = g.T <= 16 ? g.T : 16;
+  return (long long)((g.N[0] + VX - 1) / VX) * ((g.N[1] + VY - 1) / VY) * ((g.T + tchunk - 1) / tchunk);
+}
+
+bool launch_fused2d_tma(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
+                        double* socp_part, int* err, cudaStream_t s, LaunchCounter lc) {
+  FusedArgs a;
+  for (int d = 0; d < 3; ++d) {
+    a.q[d] = f.q[d];
+    a.al[d] = f.al[d];
+    a.qn[d] = fn.q[d];
+    a.aln[d] = fn.al[d];
+  }
+  a.beta = f.beta;
+  a.betan = fn.beta;
+  a.phi = f.phi;
+  a.somega = f.somega;
+  a.isg = ff_from_double(1.0 / sigma);
+  a.ts = (float)(tau * sigma);
+  a.tchunk = g.T <= 16 ? g.T : 16;
+  a.socp_part = socp_part;
+  a.err = err;
+  // beta as a 4-D tensor of 8-byte elements: (y, x, t, component)
+  CUtensorMap tm;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.N[1], (cuuint64_t)g.N[0], (cuuint64_t)g.T, (cuuint64_t)K2};
+  const cuuint64_t str[3] = {(cuuint64_t)g.N[1] * 8, (cuuint64_t)g.P * 8, (cuuint64_t)g.T * g.P * 8};
+  const cuuint32_t box[4] = {VBW, VHX, 1, K2};
+  if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, f.beta, dims, str, box)) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fused2d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemV2);
+    attr = true;
+  }
+  dim3 grid((unsigned)((g.N[0] + VX - 1) / VX), (unsigned)((g.N[1] + VY - 1) / VY),
+            (unsigned)((g.T + a.tchunk - 1) / a.tchunk));
+  k_fused2d_tma<<<grid, 256, kSmemV2, s>>>(tm, g, a);
+  lc.launched(KID_FUSED);
+  return true;
 }
 
 }  // namespace dot

@@ -38,9 +38,26 @@ __device__ __forceinline__ float grad_minus(float2 g, float q) { return (g.x - q
 
 // Line 1: b = A^*(q - alpha/sigma) - c/sigma in two-float arithmetic (alpha/sigma
 // and c/sigma are 10-10^3 times the O(1) part that survives their cancellation).
+constexpr int kMeanBlocks = kBsumParts;   // blocks of the zero-mode partial sums
+
+// FP64 sum of a block's per-thread two-float partials into out[blockIdx.x].
+__device__ __forceinline__ void block_sum_ff(float2 v, double* out) {
+  double d = ff_to_double(v);
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  __shared__ double w[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) s += w[k];
+    out[blockIdx.x] = s;
+  }
+}
+
 template <int D>
 __global__ void k_assemble_b(Geo g, MxFields f, float2 isg) {
   const long long n = (long long)(g.T + 1) * g.P;
+  float2 bsum = make_float2(0.f, 0.f);   // this thread's part of sum(b): the zero mode
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int t = plane_of(g, i);
@@ -75,46 +92,50 @@ __global__ void k_assemble_b(Geo g, MxFields f, float2 isg) {
     if (t == g.T) acc = ff_add(acc, ff_mul(f.c1[p], isg));
     f.b[i] = acc.x;
     f.blo[i] = acc.y;
+    bsum = ff_add(bsum, acc);
   }
+  block_sum_ff(bsum, f.bsum);
 }
 
-// Sum of b in FP64 (per-block partials): the exact zero mode of the right-hand
-// side.  An FP32 DCT of a field with a large mean leaks O(u_32 * mean * sqrt(n))
-// into the other coefficients; removing the exact mean from the refinement
-// residual lets the correction solve remove that leak.
-constexpr int kMeanBlocks = 304;
+// Sum of b (per-block partials, two-float per thread, FP64 per block): the exact
+// zero mode of the right-hand side.  An FP32 DCT of a field with a large mean
+// leaks O(u_32 * mean * sqrt(n)) into the other coefficients; removing the exact
+// mean from the refinement residual lets the correction solve remove that leak.
+// The iteration gets these partials from k_assemble_b; the Poisson operator entry
+// points use this kernel.
 __global__ void k_sum_b(long long n, const float* __restrict__ b, const float* __restrict__ blo,
                         double* partials) {
-  double acc = 0.0;
+  float2 acc = make_float2(0.f, 0.f);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    acc += (double)b[i] + (double)blo[i];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ double w[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) s += w[k];
-    partials[blockIdx.x] = s;
-  }
+    acc = ff_add(acc, make_float2(b[i], blo[i]));
+  block_sum_ff(acc, partials);
 }
 
 // Refinement residual r = b - mean(b) - A^*A phi1, with A^*A phi1 accumulated
 // exactly in two-float arithmetic (each neighbour difference by TwoSum; 1/h^2 is
 // an integer) and mean(b) from the FP64 partial sums.
+// mean(b) from the per-block partial sums, once, as a two-float in bsum[kMeanBlocks]
+__global__ void k_mean_b(long long n, double* bsum) {
+  __shared__ double sh[kThreads];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < kMeanBlocks; k += blockDim.x) v += bsum[k];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = sh[0] / (double)n;
+    const float hi = (float)m;
+    reinterpret_cast<float2*>(bsum + kMeanBlocks)[0] = make_float2(hi, (float)(m - (double)hi));
+  }
+}
+
 template <int D>
 __global__ void k_residual(Geo g, MxFields f, const double* bsum_partials) {
-  __shared__ float2 s_mean;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kMeanBlocks; ++k) s += bsum_partials[k];
-    const double m = s / (double)((long long)(g.T + 1) * g.P);
-    const float hi = (float)m;
-    s_mean = make_float2(hi, (float)(m - (double)hi));
-  }
-  __syncthreads();
-  const float2 mean = s_mean;
+  const float2 mean = reinterpret_cast<const float2*>(bsum_partials + kMeanBlocks)[0];
   const long long n = (long long)(g.T + 1) * g.P;
   const float* x = f.phi1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -470,11 +491,15 @@ __global__ void k_kkt_final(const double* partials, int rows, double* out, const
 // Line 2 with one refinement step: phi1 = P(b); r = b - A^*A phi1 (exact);
 // delta = P(r); out = phi1 + delta as a two-float pair.  Overwrites f.b with delta.
 template <int D>
-void poisson_refined_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out, cudaStream_t s,
-                          LaunchCounter lc) {
+void poisson_refined_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out, bool have_bsum,
+                          cudaStream_t s, LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P;
+  if (!have_bsum) {
+    k_sum_b<<<kMeanBlocks, kThreads, 0, s>>>(nn, f.b, f.blo, f.bsum);
+    lc.launched(KID_RESIDUAL);
+  }
+  k_mean_b<<<1, kThreads, 0, s>>>(nn, f.bsum);
   launch_poisson_mx(g, ps, f.b, f.phi1, s, lc);
-  k_sum_b<<<kMeanBlocks, kThreads, 0, s>>>(nn, f.b, f.blo, f.bsum);
   k_residual<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, f.bsum);
   lc.launched(KID_RESIDUAL, 2);
   launch_poisson_mx(g, ps, f.r, f.b, s, lc);
@@ -488,9 +513,9 @@ void launch_iter_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, doub
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
   const float2 isg = ff_from_double(1.0 / sigma);
   const float ts = (float)(tau * sigma);
-  k_assemble_b<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, isg);                 // line 1
+  k_assemble_b<D><<<kMeanBlocks, kThreads, 0, s>>>(g, f, isg);                   // line 1
   lc.launched(KID_ASSEMBLE_B);
-  poisson_refined_tmpl<D>(g, f, ps, f.phi, s, lc);                                // line 2
+  poisson_refined_tmpl<D>(g, f, ps, f.phi, true, s, lc);                          // line 2
   k_project<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, isg);                      // line 3
   lc.launched(KID_PROJECT);
   k_update_q0<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, isg, ts);                 // lines 4-5
@@ -523,9 +548,9 @@ void launch_iterate_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, dou
 }
 
 void launch_poisson_refined_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out,
-                               cudaStream_t s, LaunchCounter lc) {
-  if (g.D == 2) poisson_refined_tmpl<2>(g, f, ps, out, s, lc);
-  else poisson_refined_tmpl<3>(g, f, ps, out, s, lc);
+                               bool have_bsum, cudaStream_t s, LaunchCounter lc) {
+  if (g.D == 2) poisson_refined_tmpl<2>(g, f, ps, out, have_bsum, s, lc);
+  else poisson_refined_tmpl<3>(g, f, ps, out, have_bsum, s, lc);
 }
 
 void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
@@ -537,8 +562,9 @@ void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* ou
 void launch_assemble_b_mx(const Geo& g, const MxFields& f, double sigma, cudaStream_t s, LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P;
   const float2 isg = ff_from_double(1.0 / sigma);
-  if (g.D == 2) k_assemble_b<2><<<grid_for(nn), kThreads, 0, s>>>(g, f, isg);
-  else k_assemble_b<3><<<grid_for(nn), kThreads, 0, s>>>(g, f, isg);
+  (void)nn;
+  if (g.D == 2) k_assemble_b<2><<<kMeanBlocks, kThreads, 0, s>>>(g, f, isg);
+  else k_assemble_b<3><<<kMeanBlocks, kThreads, 0, s>>>(g, f, isg);
   lc.launched(KID_ASSEMBLE_B);
 }
 

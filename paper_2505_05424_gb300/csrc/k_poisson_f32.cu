@@ -99,47 +99,49 @@ __global__ void __launch_bounds__(256) k_rot_pass_f32(const float* __restrict__ 
 // 64 columns s per block.  C_t (zero-padded to Mp = 16*ceil(M/16)), the tile and
 // its transform live in shared memory; thread (tk, ts) owns rows tk + 16i and the
 // four columns 4ts..4ts+3, so each shared load feeds several FMAs.
-constexpr int kTsRowsMax = 10;   // Mp <= 160
+template <int R>
 __global__ void __launch_bounds__(256) k_tsolve_f32(Geo g, const float* __restrict__ Ct,
                                                     const float* __restrict__ lam_t, MxPoisson ps,
                                                     const float* __restrict__ X, float* __restrict__ Y) {
   extern __shared__ __align__(16) float sm[];
   const int M = g.T + 1;
-  const int Mp = (M + 15) / 16 * 16;
-  const int R = Mp / 16;
+  constexpr int Mp = 16 * R;
+  constexpr int XS = 65;          // odd row stride of the input tile: conflict-free transposed fill
   const long long S = g.P;
-  float* C = sm;                 // Mp*Mp, C[k*Mp + t]
-  float* xt = C + Mp * Mp;       // Mp*64: xt[t][s]
-  float* yt = xt + Mp * 64;      // Mp*64
+  float* C = sm;                  // Mp*Mp, C[k*Mp + t]
+  float* xt = C + Mp * Mp;        // Mp*XS: xt[t*XS + s]
+  float* yt = xt + Mp * XS;       // Mp*64: yt[k*64 + s]
   const long long s0 = (long long)blockIdx.x * 64;
   for (int e = threadIdx.x; e < Mp * Mp; e += blockDim.x) {
     const int k = e / Mp, t = e % Mp;
     C[e] = (k < M && t < M) ? Ct[k * M + t] : 0.f;
   }
-  for (int e = threadIdx.x; e < Mp * 64; e += blockDim.x) {
-    const int s = e / Mp, t = e % Mp;   // consecutive threads read consecutive t of one column
-    const long long col = s0 + s;
-    xt[t * 64 + s] = (col < S && t < M) ? X[col * M + t] : 0.f;
+  // the tile's 64 columns are 64*M contiguous floats: read them linearly
+  const long long ncol = (S - s0) < 64 ? (S - s0) : 64;
+  for (int e = threadIdx.x; e < 64 * M; e += blockDim.x) {
+    const int s = e / M, t = e - s * M;
+    xt[t * XS + s] = s < ncol ? X[s0 * M + e] : 0.f;
   }
+  for (int e = threadIdx.x; e < (Mp - M) * 64; e += blockDim.x) xt[(M + e / 64) * XS + e % 64] = 0.f;
   __syncthreads();
   const int tk = threadIdx.x >> 4, ts = threadIdx.x & 15;
-  float acc[kTsRowsMax][4];
+  float acc[R][4];
   // forward DCT-II along t
 #pragma unroll
-  for (int i = 0; i < kTsRowsMax; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
   for (int t = 0; t < Mp; ++t) {
-    const float4 b = *reinterpret_cast<const float4*>(&xt[t * 64 + 4 * ts]);
+    const float* xr = &xt[t * XS + 4 * ts];
+    const float b0 = xr[0], b1 = xr[1], b2 = xr[2], b3 = xr[3];
 #pragma unroll
-    for (int i = 0; i < kTsRowsMax; ++i) {
-      if (i < R) {
-        const float a = C[(tk + 16 * i) * Mp + t];
-        acc[i][0] = fmaf(a, b.x, acc[i][0]);
-        acc[i][1] = fmaf(a, b.y, acc[i][1]);
-        acc[i][2] = fmaf(a, b.z, acc[i][2]);
-        acc[i][3] = fmaf(a, b.w, acc[i][3]);
-      }
+    for (int i = 0; i < R; ++i) {
+      const float a = C[(tk + 16 * i) * Mp + t];
+      acc[i][0] = fmaf(a, b0, acc[i][0]);
+      acc[i][1] = fmaf(a, b1, acc[i][1]);
+      acc[i][2] = fmaf(a, b2, acc[i][2]);
+      acc[i][3] = fmaf(a, b3, acc[i][3]);
     }
   }
   // scale by 1/lambda(k, s); the zero mode (k = 0, s = 0) is set to 0
@@ -149,37 +151,34 @@ __global__ void __launch_bounds__(256) k_tsolve_f32(Geo g, const float* __restri
     float lsp = 0.f;
     for (int d = 0; d < g.D; ++d) lsp += ps.lam[1 + d][coord(g, col < S ? col : 0, d)];
 #pragma unroll
-    for (int i = 0; i < kTsRowsMax; ++i) {
-      if (i < R) {
-        const int k = tk + 16 * i;
-        const float lam = (k < M ? lam_t[k] : 1.f) + lsp;
-        yt[k * 64 + 4 * ts + j] = (k == 0 && col == 0) ? 0.f : acc[i][j] / lam;
-      }
+    for (int i = 0; i < R; ++i) {
+      const int k = tk + 16 * i;
+      const float lam = (k < M ? lam_t[k] : 1.f) + lsp;
+      yt[k * 64 + 4 * ts + j] = (k == 0 && col == 0) ? 0.f : acc[i][j] / lam;
     }
   }
   __syncthreads();
   // inverse DCT-III along t: out[t][s] = sum_k C[k][t] yt[k][s]
 #pragma unroll
-  for (int i = 0; i < kTsRowsMax; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
   for (int k = 0; k < Mp; ++k) {
     const float4 b = *reinterpret_cast<const float4*>(&yt[k * 64 + 4 * ts]);
 #pragma unroll
-    for (int i = 0; i < kTsRowsMax; ++i) {
-      if (i < R) {
-        const float a = C[k * Mp + tk + 16 * i];
-        acc[i][0] = fmaf(a, b.x, acc[i][0]);
-        acc[i][1] = fmaf(a, b.y, acc[i][1]);
-        acc[i][2] = fmaf(a, b.z, acc[i][2]);
-        acc[i][3] = fmaf(a, b.w, acc[i][3]);
-      }
+    for (int i = 0; i < R; ++i) {
+      const float a = C[k * Mp + tk + 16 * i];
+      acc[i][0] = fmaf(a, b.x, acc[i][0]);
+      acc[i][1] = fmaf(a, b.y, acc[i][1]);
+      acc[i][2] = fmaf(a, b.z, acc[i][2]);
+      acc[i][3] = fmaf(a, b.w, acc[i][3]);
     }
   }
 #pragma unroll
-  for (int i = 0; i < kTsRowsMax; ++i) {
+  for (int i = 0; i < R; ++i) {
     const int t = tk + 16 * i;
-    if (i >= R || t >= M) continue;
+    if (t >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const long long col = s0 + 4 * ts + j;
@@ -209,7 +208,34 @@ void spatial_pass(const MxPoisson& ps, int axis, bool inverse, const float* X, f
 
 size_t tsolve_smem_bytes(const Geo& g) {
   const size_t Mp = ((size_t)g.T + 1 + 15) / 16 * 16;
-  return (Mp * Mp + 2 * Mp * 64) * sizeof(float);
+  return (Mp * Mp + Mp * 65 + Mp * 64) * sizeof(float);
+}
+
+template <int R>
+void launch_tsolve_r(const Geo& g, const MxPoisson& ps, const float* X, float* Y, cudaStream_t s) {
+  const size_t sm = tsolve_smem_bytes(g);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tsolve_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  k_tsolve_f32<R><<<(unsigned)((g.P + 63) / 64), 256, sm, s>>>(g, ps.C[0], ps.lam[0], ps, X, Y);
+}
+
+// the time-axis pass, specialised on the number of 16-row groups of the padded axis
+void launch_tsolve(const Geo& g, const MxPoisson& ps, const float* X, float* Y, cudaStream_t s) {
+  switch ((g.T + 1 + 15) / 16) {
+    case 1: launch_tsolve_r<1>(g, ps, X, Y, s); break;
+    case 2: launch_tsolve_r<2>(g, ps, X, Y, s); break;
+    case 3: launch_tsolve_r<3>(g, ps, X, Y, s); break;
+    case 4: launch_tsolve_r<4>(g, ps, X, Y, s); break;
+    case 5: launch_tsolve_r<5>(g, ps, X, Y, s); break;
+    case 6: launch_tsolve_r<6>(g, ps, X, Y, s); break;
+    case 7: launch_tsolve_r<7>(g, ps, X, Y, s); break;
+    case 8: launch_tsolve_r<8>(g, ps, X, Y, s); break;
+    case 9: launch_tsolve_r<9>(g, ps, X, Y, s); break;
+    default: launch_tsolve_r<10>(g, ps, X, Y, s); break;
+  }
 }
 
 void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
@@ -227,13 +253,7 @@ void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, floa
   }
   {
     const int nx = next();
-    const size_t sm = tsolve_smem_bytes(g);
-    static size_t attr = 0;
-    if (sm > 48 * 1024 && sm > attr) {
-      cudaFuncSetAttribute(k_tsolve_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = sm;
-    }
-    k_tsolve_f32<<<(unsigned)((g.P + 63) / 64), 256, sm, s>>>(g, ps.C[0], ps.lam[0], ps, cur(), w[nx]);
+    launch_tsolve(g, ps, cur(), w[nx], s);
     lc.launched(KID_SCALE);
     ci = nx;
   }

@@ -1,6 +1,7 @@
 // path_mixed.cu -- the mixed-precision path of Algorithm 2 (see k_mixed.cu for
 // the storage and arithmetic of each field).  Host side: buffer plan, uploads,
 // and the double <-> (float | two-float) conversions of the C ABI's host arrays.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -56,7 +57,7 @@ void carve_mx(const Geo& g, Carver& cv, MxBuffers* B) {
     }
     B->f2.beta = cv.take<float2>((size_t)g.K * n0);
     B->f.z = nullptr;                       // z never leaves the fused kernel
-    B->socp = cv.take<double>((size_t)fused2d_blocks(g));
+    B->socp = cv.take<double>((size_t)std::max(fused2d_blocks(g), fused2d_tma_blocks(g)));
   } else {
     B->f.z = cv.take<float>((size_t)g.K * n0);
     B->socp = nullptr;
@@ -67,7 +68,7 @@ void carve_mx(const Geo& g, Carver& cv, MxBuffers* B) {
   B->f.blo = cv.take<float>(nn);
   B->f.phi1 = cv.take<float>(nn);
   B->f.r = cv.take<float>(nn);
-  B->f.bsum = cv.take<double>(304);
+  B->f.bsum = cv.take<double>(kBsumParts + 2);
   B->ps.w1 = cv.take<float>(nn);
   B->ps.w2 = cv.take<float>(nn);
   B->c0 = cv.take<float2>(P);
@@ -182,6 +183,7 @@ class PathMixed : public Path {
     B_.ps.err = B_.err;
     B_.ps.use_tc = true;
     fused_ = fused2d_supported(g_);
+    tma_ = fused_ && fused2d_tma_supported(g_);
     sync_shared();
     if (e == cudaSuccess) e = cudaMemsetAsync(B_.err, 0, 64 * sizeof(int), s);
     if (g_.T + 1 > 160) {
@@ -198,8 +200,9 @@ class PathMixed : public Path {
       const MxFields& fc = cur();
       const MxFields& fn = other();
       launch_assemble_b_mx(g_, fc, sigma, s, lc);                           // line 1
-      launch_poisson_refined_mx(g_, fc, B_.ps, fc.phi, s, lc);               // line 2 (+ refinement)
-      launch_fused2d(g_, fc, fn, sigma, tau, B_.socp, s, lc);                // lines 3-6
+      launch_poisson_refined_mx(g_, fc, B_.ps, fc.phi, true, s, lc);         // line 2 (+ refinement)
+      if (!(tma_ && launch_fused2d_tma(g_, fc, fn, sigma, tau, B_.socp, B_.err, s, lc)))
+        launch_fused2d(g_, fc, fn, sigma, tau, B_.socp, s, lc);              // lines 3-6
       cur_ ^= 1;
     } else {
       launch_iterate_mx(g_, B_.f, B_.ps, sigma, tau, s, lc);
@@ -208,7 +211,7 @@ class PathMixed : public Path {
 
   void kkt(cudaStream_t s, LaunchCounter lc) override {
     launch_kkt_mx(g_, cur(), B_.partials, B_.red, fused_ ? B_.socp : nullptr,
-                  fused_ ? (int)fused2d_blocks(g_) : 0, s, lc);
+                  fused_ ? (int)(tma_ ? fused2d_tma_blocks(g_) : fused2d_blocks(g_)) : 0, s, lc);
   }
   const double* red_out() const override { return B_.red; }
   const int* error_flag() const override { return B_.err; }
@@ -315,7 +318,7 @@ class PathMixed : public Path {
     cudaError_t e = up(B_.f.b, tb.data(), nn * 4, s);
     if (e == cudaSuccess) e = up(B_.f.blo, tl.data(), nn * 4, s);
     if (e == cudaSuccess) {
-      launch_poisson_refined_mx(g_, B_.f, B_.ps, B_.phi_op, s, lc);
+      launch_poisson_refined_mx(g_, B_.f, B_.ps, B_.phi_op, false, s, lc);
       e = cudaGetLastError();
     }
     std::vector<float2> t(nn);
@@ -350,7 +353,7 @@ class PathMixed : public Path {
     }
     if (e == cudaSuccess && B_.f.z) e = cudaMemsetAsync(B_.f.z, 0, (size_t)g_.K * n0 * 4, s);
     if (e == cudaSuccess && B_.socp)
-      e = cudaMemsetAsync(B_.socp, 0, (size_t)fused2d_blocks(g_) * sizeof(double), s);
+      e = cudaMemsetAsync(B_.socp, 0, (size_t)std::max(fused2d_blocks(g_), fused2d_tma_blocks(g_)) * sizeof(double), s);
     return e;
   }
 
@@ -416,6 +419,7 @@ class PathMixed : public Path {
   Geo g_;
   MxBuffers B_;
   bool fused_ = false;
+  bool tma_ = false;
   int cur_ = 0;
   std::vector<float2> hc0_, hc1_;
   std::vector<float> hom_, hsom_;
