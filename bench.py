@@ -30,8 +30,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/s at KKT<=1e-6, mixed vs FP64 on same GPU; p50/p99 latency; %HBM peak"
 WORKLOAD = "mix256"
-WORKLOAD_DESC = ("2D DOT 256x256 cells x 64 time steps, seeded mixtures of 1-5 Gaussians "
-                 "(means U[0.15,0.85]^2, sigma U[0.03,0.12], Dirichlet weights), pdf < 1e-4 -> 0")
+WORKLOAD_DESCS = {
+    "mix256": ("2D DOT 256x256 cells x 64 time steps, seeded mixtures of 1-5 Gaussians "
+               "(means U[0.15,0.85]^2, sigma U[0.03,0.12], Dirichlet weights), pdf < 1e-4 -> 0"),
+    "obst128": ("2D DOT with obstacles, 128x128 cells x 32 time steps, seeded mixtures as mix256 zeroed on "
+                "a mask of 3-6 rectangles covering 8-12% of cells, obstacle weight 1e-6"),
+    "mix3d64": ("3D DOT 64^3 cells x 32 time steps, seeded mixtures of 2-4 anisotropic Gaussians "
+                "(sigma U[0.05,0.15]^3), floor 1e-4"),
+    "gauss32": "2D DOT 32x32 cells x 16 time steps, Gaussians sigma 0.1 at (0.3,0.3), (0.7,0.7) + floor 1e-3",
+}
+WORKLOAD_SEEDS = {"mix256": 1002, "obst128": 1003, "mix3d64": 1004, "gauss32": None}
 # Iterations the FP64 recurrence (GPU FP64 path == oracle, lock-step tested) needs to reach
 # eta_dot <= 1e-6 on the seed-1002 instance of this workload; converts the oracle's
 # seconds per iteration into solves/s in the reference arm.  Measured by this script's
@@ -53,6 +61,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64"])
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serve the first SERVE requests of the seeded serving stream (2D grids "
+                         "{32^2x16, 64^2x32, 128^2x32, 256^2x64}, Poisson arrivals, 20%% masked) through "
+                         "the continuous-batching server and print its JSON line instead")
+    ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the serving stream")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="run this many iterations of one solve (no stopping checks) and exit: a short, "
                          "fixed launch sequence for ncu; prints no JSON")
@@ -169,6 +182,28 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
 NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"): 594.088448e6 + 451.743232e6}
 
 
+# ---- replicas: one process per GPU, independent solves, no data-path collective --
+
+def replica_seed(base: int, step: int, rank: int) -> int:
+    """Seed of the instance a rank solves at a step: ranks never share an instance."""
+    return base + step + 1000 * rank
+
+
+def replica_max_ms(elapsed_ms: float, dist=None, device=None) -> float:
+    """The slowest rank's timed region (the job ends when every replica has)."""
+    if dist is None:
+        return float(elapsed_ms)
+    import torch
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, steps: int, max_ms: float) -> float:
+    """Whole-job solves/s: all ranks' solves over the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
+
+
 def make_solver(spec, r0, r1, mask, prec, **kw):
     from paper_2505_05424_gb300.solver import DotSolver
     return DotSolver(spec.D, spec.T, spec.N, r0, r1, mask=mask, prec=prec, **kw)
@@ -197,10 +232,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    spec = W.MIX256
+    wl = args.workload
+    spec = W.workload(wl)[0]
+    base_seed = WORKLOAD_SEEDS[wl]
+
     def instance(step):
-        r0, r1, m = W.mixture_pair(spec, 1002 + step + 1000 * rank)
-        return r0, r1, m
+        if base_seed is None:
+            return W.workload(wl)[1:]
+        return W.workload(wl, replica_seed(base_seed, step, rank))[1:]
 
     stream = torch.cuda.current_stream(dev)
     # warm-up solves
@@ -238,11 +277,7 @@ def run_ours(args):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = replica_max_ms(ev0.elapsed_time(ev1), dist, dev)
     gpu_launches = sum(s.launch_count() for s in solvers) - launches0
     prof = {}
     for s in solvers:
@@ -252,7 +287,7 @@ def run_ours(args):
             a[1] += n
     for s in solvers:
         s.close()
-    value = world * args.steps / (elapsed_ms / 1e3)
+    value = replica_value(world, args.steps, elapsed_ms)
     if rank != 0:
         if dist is not None:
             dist.barrier()
@@ -276,7 +311,7 @@ def run_ours(args):
     else:
         achieved = abytes / (per_launch_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
-        traffic = NCU_TRAFFIC.get((dname, WORKLOAD, args.prec))
+        traffic = NCU_TRAFFIC.get((dname, wl, args.prec))
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": dname,
                 "per_launch_ms": round(per_launch_ms, 5), "algorithmic_bytes": abytes,
@@ -311,9 +346,9 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "D": spec.D, "T": spec.T, "N": spec.N,
+        "config": {"workload": f"{wl}: {WORKLOAD_DESCS[wl]}", "D": spec.D, "T": spec.T, "N": spec.N,
                    "tol": args.tol, "prec": args.prec, "check_every": 10, "tau": 1.9,
-                   "l2": "inputs larger than L2 (per-solve state > 129 MB)", "seeds": "1002+step",
+                   "l2": "inputs larger than L2 (per-solve state > 129 MB)", "seeds": f"{base_seed}+step",
                    "parallelism": f"replicas{world}"},
         "iterations": iters, "eta_dot": etas, "objective": objs,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -347,7 +382,7 @@ def run_ours(args):
         if rc == 0:
             out["mixed_vs_fp64"] = round(value / (1.0 / dt), 3)
 
-    if not args.no_cpu:
+    if not args.no_cpu and wl == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(fp64_iters or (iters[0] if iters else None))
     print(json.dumps(out))
     if dist is not None:
@@ -396,10 +431,85 @@ def run_reference(args):
     out = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": spi * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "tol": args.tol},
+           "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESCS[WORKLOAD]}", "tol": args.tol},
            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
                             "sample": f"each step = 1 oracle iteration; solves/s = 1/(s/it x {iters})"},
            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+SERVE_GRIDS = ((32, 16), (64, 32), (128, 32), (256, 64))
+
+
+def serving_stream(n: int, rate: float, seed: int = 5005):
+    """The first n requests of the seeded serving stream: (arrival s, N, T, seed, masked)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        N, T = SERVE_GRIDS[int(rng.integers(0, len(SERVE_GRIDS)))]
+        out.append((t, N, T, 50000 + i, bool(rng.random() < 0.2)))
+    return out
+
+
+def run_serve(args):
+    """Serve the stream through DotServer; latency = completion - submission."""
+    import torch
+    from paper_2505_05424_gb300 import workloads as W
+    from paper_2505_05424_gb300 import _native
+    from paper_2505_05424_gb300.solver import DotServer
+    _native.build()
+    _native.load()
+    torch.cuda.init()
+    reqs = serving_stream(args.serve, args.rate)
+    inputs = [W.mixture_pair(W.GridSpec(2, T, N), sd, obstacles=m) for (_, N, T, sd, m) in reqs]
+    # warm-up: one solve per grid (kernel attributes, graph capture paths)
+    with DotServer() as srv:
+        ids = [srv.submit(2, T, N, *W.mixture_pair(W.GridSpec(2, T, N), 7)[:2], tol=args.tol, maxit=40,
+                          keep_fields=False) for (N, T) in SERVE_GRIDS]
+        for i in ids:
+            srv.wait(i)
+    clocks = ClockSampler(0)
+    srv = DotServer()
+    clocks.start()
+    t0 = time.perf_counter()
+    ids = []
+    for (ta, N, T, sd, m), (r0, r1, mask) in zip(reqs, inputs):
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(2, T, N, r0, r1, mask=mask, tol=args.tol, maxit=args.maxit, keep_fields=False))
+    status = [srv.wait(i) for i in ids]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    res = [srv.result(i) for i in ids]
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([r["times"][2] - r["times"][0] for r in res]) * 1e3
+    qwait = np.array([r["times"][1] - r["times"][0] for r in res]) * 1e3
+    t_first = min(r["times"][0] for r in res)
+    t_last = max(r["times"][2] for r in res)
+    per_grid = {}
+    for (ta, N, T, sd, m), l, r in zip(reqs, lat, res):
+        d = per_grid.setdefault(f"{N}^2x{T}", {"n": 0, "lat": [], "iters": []})
+        d["n"] += 1
+        d["lat"].append(float(l))
+        d["iters"].append(int(r["kkt"]["iterations"]))
+    for k, d in per_grid.items():
+        d["p50_ms"] = float(np.percentile(d["lat"], 50))
+        d["p99_ms"] = float(np.percentile(d["lat"], 99))
+        d["mean_iters"] = float(np.mean(d["iters"]))
+        del d["lat"], d["iters"]
+    out = {"metric": "serving: solves/s and p50/p99 latency, seeded stream of mixed 2D grids, KKT<=1e-6",
+           "value": round(len(ids) / (t_last - t_first), 4), "unit": "solves/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"serving stream, first {len(ids)} requests, Poisson arrivals at {args.rate}/s, "
+                                  "grids uniform over 32^2x16, 64^2x32, 128^2x32, 256^2x64, 20% with rectangle "
+                                  "obstacles, seeded mixtures (seed 50000+i)", "tol": args.tol},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "queue_p50": float(np.percentile(qwait, 50)), "queue_p99": float(np.percentile(qwait, 99))},
+           "converged": int(sum(1 for s_ in status if s_ == 0)), "requests": len(ids),
+           "wall_s": round(wall, 3), "per_grid": per_grid, "server": stats, "clocks": clk}
     print(json.dumps(out))
 
 
@@ -407,6 +517,9 @@ def main():
     args = parse()
     if args.profile_iters > 0:
         run_profile_case(args)
+        return
+    if args.serve > 0:
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -182,6 +182,66 @@ const char *dot_last_error(const dot_ctx *ctx);
 const char *dot_version(void);
 long dot_launch_count(const dot_ctx *ctx);
 
+/* ---- Serving: many solves advanced together (continuous batching) -----------
+ *
+ * The paper solves one problem at a time; this layer runs Algorithm 2 for many
+ * independent DOT problems on one GPU.  Requests of the same grid share a batch:
+ * a device workspace holding G solves whose per-iteration kernels advance every
+ * active slot in one launch (one CUDA graph per batch covers check_every
+ * iterations and the stopping measures).  After each such period the server
+ * thread applies the stopping test and the penalty rule of Sec. 5.3 to every
+ * slot, retires the slots that finished and admits queued requests into free
+ * slots; a request for a grid with no free slot gets a new batch if its
+ * workspace fits the memory budget, otherwise it waits (admission by device
+ * memory footprint).  Batches of different grids run on separate streams and
+ * overlap on the device.  Every slot runs the same recurrence, schedule and
+ * kernels as a dot_create/dot_solve context of precision DOT_MIXED, so a
+ * request's result does not depend on which other requests share its batch.
+ *
+ * Grids: D = 2 with every axis (T+1 and each N_d) at most 256 and N_d a
+ * multiple of 4 are batched; other grids get batches of one slot.
+ * Threading: every function may be called from any thread. */
+typedef struct dot_server dot_server;
+
+typedef struct {
+  size_t hbm_budget;   /* device bytes the batches may hold; 0 = 80% of free memory at creation */
+  int max_slots;       /* most solves in one batch (1..256; default 64) */
+  long target_nodes;   /* a batch gets about this many grid nodes, (T+1) N_1..N_D per slot,
+                          within [1, max_slots] slots (default 4,194,304) */
+  int use_graphs;      /* 1: one captured CUDA graph per batch and period (default); 0: plain launches */
+  int idle_ms;         /* a batch with no solve for this long returns its memory (default 200) */
+} dot_server_options;
+
+void dot_server_default_options(dot_server_options *o);
+/* opt: algorithm options (NULL = defaults; prec must be DOT_MIXED); sopt: NULL = defaults.
+ * Starts the server thread on the calling thread's current device. */
+int dot_server_create(const dot_options *opt, const dot_server_options *sopt, dot_server **out);
+/* Queue a solve.  rho0, rho1, mask as for dot_create (copied before the call
+ * returns); tol, maxit as for dot_solve; keep_fields: 1 = keep rho, m, phi for
+ * dot_server_result, 0 = only the objective and the stopping measures.
+ * *id receives the request id (> 0). */
+int dot_server_submit(dot_server *srv, const dot_grid *grid, const double *rho0, const double *rho1,
+                      const uint8_t *mask, double tol, long maxit, int keep_fields, long long *id);
+/* Wait up to timeout_s seconds (< 0: forever, 0: poll) for request id.  Returns
+ * DOT_OK when it has finished, with its solve status (as dot_solve's return) in
+ * *status; DOT_ETIMEOUT when it has not; DOT_EINVAL for an unknown id. */
+int dot_server_wait(dot_server *srv, long long id, double timeout_s, int *status);
+/* Results of a finished request (any pointer may be NULL): rho, m, phi as for
+ * dot_get (only with keep_fields), objective, kkt[DOT_KKT_LEN], and times[3] =
+ * seconds since the server started at submission, admission and completion. */
+int dot_server_result(dot_server *srv, long long id, double *rho, double *m, double *phi, double *objective,
+                      double *kkt, double *times);
+/* Forget a finished request and free its host copies. */
+int dot_server_release(dot_server *srv, long long id);
+/* Counters: out[0] queued, [1] running, [2] finished, [3] batches, [4] device
+ * bytes held, [5] graph (or period) launches, [6] kernel launches, [7] most solves
+ * running at once, [8] most batches at once.  Returns the number written (<= n). */
+int dot_server_stats(dot_server *srv, double *out, int n);
+/* Stops the server thread (queued and running requests are abandoned) and frees
+ * every device buffer. */
+void dot_server_destroy(dot_server *srv);
+const char *dot_server_last_error(const dot_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,11 @@ class DotOptions(ctypes.Structure):
                 ("obstacle_weight", ctypes.c_double), ("max_seconds", ctypes.c_double)]
 
 
+class DotServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("target_nodes", ctypes.c_long),
+                ("use_graphs", ctypes.c_int), ("idle_ms", ctypes.c_int)]
+
+
 DOT_OK, DOT_EINVAL, DOT_ENOMEM, DOT_ECUDA, DOT_EDIVERGED, DOT_ETIMEOUT, DOT_ENOTCONV = 0, -1, -2, -3, -4, -5, 1
 DOT_FP64, DOT_MIXED = 0, 1
 KKT_NAMES = ("eta_dot", "eta_P", "eta_D", "eta_C", "eta_P_soc", "eta_D_soc", "primal_obj", "dual_obj",
@@ -92,7 +97,9 @@ DOT_KKT_LEN = len(KKT_NAMES)
 EXPORTS = ("dot_default_options", "dot_workspace_bytes", "dot_create", "dot_solve", "dot_get", "dot_kkt",
            "dot_get_state", "dot_set_state", "dot_poisson", "dot_destroy", "dot_last_error", "dot_version",
            "dot_launch_count", "dot_profile", "dot_profile_read", "dot_kernel_name", "dot_poisson_f32_noalloc",
-           "dot_noalloc_last_error")
+           "dot_noalloc_last_error", "dot_server_default_options", "dot_server_create", "dot_server_submit",
+           "dot_server_wait", "dot_server_result", "dot_server_release", "dot_server_stats",
+           "dot_server_destroy", "dot_server_last_error")
 
 _lib = None
 _lock = threading.Lock()
@@ -149,5 +156,24 @@ def load(build_if_missing: bool = True):
         lib.dot_poisson_f32_noalloc.restype = ctypes.c_int
         lib.dot_noalloc_last_error.argtypes = []
         lib.dot_noalloc_last_error.restype = ctypes.c_char_p
+        lib.dot_server_default_options.argtypes = [P(DotServerOptions)]
+        lib.dot_server_default_options.restype = None
+        lib.dot_server_create.argtypes = [P(DotOptions), P(DotServerOptions), P(vp)]
+        lib.dot_server_create.restype = ctypes.c_int
+        lib.dot_server_submit.argtypes = [vp, P(DotGrid), dp, dp, P(ctypes.c_uint8), ctypes.c_double, ctypes.c_long,
+                                          ctypes.c_int, P(ctypes.c_longlong)]
+        lib.dot_server_submit.restype = ctypes.c_int
+        lib.dot_server_wait.argtypes = [vp, ctypes.c_longlong, ctypes.c_double, P(ctypes.c_int)]
+        lib.dot_server_wait.restype = ctypes.c_int
+        lib.dot_server_result.argtypes = [vp, ctypes.c_longlong, dp, dp, dp, dp, dp, dp]
+        lib.dot_server_result.restype = ctypes.c_int
+        lib.dot_server_release.argtypes = [vp, ctypes.c_longlong]
+        lib.dot_server_release.restype = ctypes.c_int
+        lib.dot_server_stats.argtypes = [vp, dp, ctypes.c_int]
+        lib.dot_server_stats.restype = ctypes.c_int
+        lib.dot_server_destroy.argtypes = [vp]
+        lib.dot_server_destroy.restype = None
+        lib.dot_server_last_error.argtypes = [vp]
+        lib.dot_server_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib

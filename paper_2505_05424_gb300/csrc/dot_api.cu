@@ -65,6 +65,88 @@ Geo dot::make_geo(const dot_grid& gr) {
   return g;
 }
 
+// Stopping measures from the reduction slots (Sec. 5.3), discrete L2 norms with
+// the space-time cell volume h_0 h_1 ... h_D.
+void dot::kkt_measures(const Geo& g, double cn2, const double* r, long iters, double sigma, double* kkt) {
+  double vol = 1.0 / g.T;
+  for (int d = 0; d < g.D; ++d) vol *= 1.0 / g.N[d];
+  auto L2 = [vol](double s) { return std::sqrt(vol * s); };
+  const double dn2 = 2.0 * (double)g.T * (double)g.P;
+  const double etaP = L2(r[R_PRIM]) / (1.0 + L2(r[R_APHI]) + L2(r[R_Q]));
+  const double etaD = L2(r[R_DUALRES]) / (1.0 + L2(cn2));
+  const double c1 = L2(r[R_COMP0]) / (1.0 + L2(r[R_ALPHA0]) + L2(r[R_F]));
+  const double c2 = L2(r[R_COMPD]) / (1.0 + L2(r[R_ALPHAB]) + L2(r[R_G]));
+  const double etaC = c1 > c2 ? c1 : c2;
+  const double psoc = L2(r[R_SOCP]) / (1.0 + L2(dn2));
+  const double dsoc = L2(r[R_SOCD]) / (1.0 + L2(r[R_FBB]) + L2(r[R_ALPHA0] + r[R_ALPHAB]));
+  double eta = etaP;
+  if (etaD > eta) eta = etaD;
+  if (etaC > eta) eta = etaC;
+  if (std::isnan(etaD) || std::isnan(etaC) || std::isnan(etaP)) eta = NAN;
+  kkt[DOT_KKT_ETA] = eta;
+  kkt[DOT_KKT_ETA_P] = etaP;
+  kkt[DOT_KKT_ETA_D] = etaD;
+  kkt[DOT_KKT_ETA_C] = etaC;
+  kkt[DOT_KKT_ETA_P_SOC] = etaP > psoc ? etaP : psoc;
+  kkt[DOT_KKT_ETA_D_SOC] = etaD > dsoc ? etaD : dsoc;
+  kkt[DOT_KKT_PRIMAL] = r[R_CPHI];
+  kkt[DOT_KKT_DUAL] = r[R_DUALOBJ];
+  kkt[DOT_KKT_GAP] = std::fabs(r[R_CPHI] - r[R_DUALOBJ]) / (1.0 + std::fabs(r[R_CPHI]) + std::fabs(r[R_DUALOBJ]));
+  kkt[DOT_KKT_ITERS] = (double)iters;
+  kkt[DOT_KKT_SIGMA] = sigma;
+}
+
+// Validate the densities and the mask and turn them into c of eq. (defc) as
+// cell-average densities (mass / (h_1 ... h_D), each density normalised to mass
+// 1: the data scaling of Sec. 5.3; it leaves phi and q unchanged and makes
+// alpha_0 / h_0 the density) and the obstacle weights omega.
+int dot::prepare_densities(const Geo& g, const double* rho0, const double* rho1, const uint8_t* mask,
+                           double obstacle_weight, std::vector<double>* m0, std::vector<double>* m1,
+                           std::vector<double>* omega, bool* any_mask, std::string* why) {
+  const long long P = g.P;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long i = 0; i < P; ++i) {
+    if (!std::isfinite(rho0[i]) || !std::isfinite(rho1[i]) || rho0[i] < 0.0 || rho1[i] < 0.0) {
+      *why = "densities must be finite and non-negative";
+      return DOT_EINVAL;
+    }
+    s0 += rho0[i];
+    s1 += rho1[i];
+  }
+  if (!(s0 > 0.0) || !(s1 > 0.0) || !std::isfinite(s0) || !std::isfinite(s1)) {
+    *why = "densities must have positive finite mass";
+    return DOT_EINVAL;
+  }
+  m0->resize(P);
+  m1->resize(P);
+  omega->resize(P);
+  *any_mask = false;
+  const double inv_cell = (double)P;
+  for (long long i = 0; i < P; ++i) {
+    (*m0)[i] = rho0[i] / s0 * inv_cell;
+    (*m1)[i] = rho1[i] / s1 * inv_cell;
+    const bool ob = mask && mask[i];
+    *any_mask = *any_mask || ob;
+    (*omega)[i] = ob ? obstacle_weight : 1.0;
+  }
+  return DOT_OK;
+}
+
+bool dot::grid_valid(const dot_grid* g, std::string* why) { return grid_ok(g, why); }
+
+int dot::check_options(const dot_options& o, std::string* why) {
+  if (!(o.tau > 0.0 && o.tau < 2.0)) { *why = "tau must lie in (0, 2)"; return DOT_EINVAL; }
+  if (!(o.sigma0 > 0.0 && std::isfinite(o.sigma0))) { *why = "sigma0 must be > 0"; return DOT_EINVAL; }
+  if (!(o.s_sigma > 1.0) || !(o.s_r > 1.0)) { *why = "s_sigma and s_r must be > 1"; return DOT_EINVAL; }
+  if (o.check_every < 0) { *why = "check_every must be >= 0"; return DOT_EINVAL; }
+  if (!(o.obstacle_weight > 0.0 && std::isfinite(o.obstacle_weight))) {
+    *why = "obstacle_weight must be > 0";
+    return DOT_EINVAL;
+  }
+  if (o.prec != DOT_FP64 && o.prec != DOT_MIXED) { *why = "unknown precision"; return DOT_EINVAL; }
+  return DOT_OK;
+}
+
 struct dot_ctx {
   dot_grid grid;
   dot_options opt;
@@ -150,39 +232,11 @@ int cuda_fail(dot_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-// Stopping measures from the reduction slots (Sec. 5.3), discrete L2 norms with
-// the space-time cell volume h_0 h_1 ... h_D.
 void finish_kkt(dot_ctx* c, const double* r) {
-  const Geo& g = c->geo;
-  double vol = 1.0 / g.T;
-  for (int d = 0; d < g.D; ++d) vol *= 1.0 / g.N[d];
-  auto L2 = [vol](double s) { return std::sqrt(vol * s); };
   double cn2 = 0.0;
   for (double v : c->m0) cn2 += v * v;
   for (double v : c->m1) cn2 += v * v;
-  const double dn2 = 2.0 * (double)g.T * (double)g.P;
-  const double etaP = L2(r[R_PRIM]) / (1.0 + L2(r[R_APHI]) + L2(r[R_Q]));
-  const double etaD = L2(r[R_DUALRES]) / (1.0 + L2(cn2));
-  const double c1 = L2(r[R_COMP0]) / (1.0 + L2(r[R_ALPHA0]) + L2(r[R_F]));
-  const double c2 = L2(r[R_COMPD]) / (1.0 + L2(r[R_ALPHAB]) + L2(r[R_G]));
-  const double etaC = c1 > c2 ? c1 : c2;
-  const double psoc = L2(r[R_SOCP]) / (1.0 + L2(dn2));
-  const double dsoc = L2(r[R_SOCD]) / (1.0 + L2(r[R_FBB]) + L2(r[R_ALPHA0] + r[R_ALPHAB]));
-  double eta = etaP;
-  if (etaD > eta) eta = etaD;
-  if (etaC > eta) eta = etaC;
-  if (std::isnan(etaD) || std::isnan(etaC) || std::isnan(etaP)) eta = NAN;
-  c->kkt[DOT_KKT_ETA] = eta;
-  c->kkt[DOT_KKT_ETA_P] = etaP;
-  c->kkt[DOT_KKT_ETA_D] = etaD;
-  c->kkt[DOT_KKT_ETA_C] = etaC;
-  c->kkt[DOT_KKT_ETA_P_SOC] = etaP > psoc ? etaP : psoc;
-  c->kkt[DOT_KKT_ETA_D_SOC] = etaD > dsoc ? etaD : dsoc;
-  c->kkt[DOT_KKT_PRIMAL] = r[R_CPHI];
-  c->kkt[DOT_KKT_DUAL] = r[R_DUALOBJ];
-  c->kkt[DOT_KKT_GAP] = std::fabs(r[R_CPHI] - r[R_DUALOBJ]) / (1.0 + std::fabs(r[R_CPHI]) + std::fabs(r[R_DUALOBJ]));
-  c->kkt[DOT_KKT_ITERS] = (double)c->iters;
-  c->kkt[DOT_KKT_SIGMA] = c->sigma;
+  kkt_measures(c->geo, cn2, r, c->iters, c->sigma, c->kkt);
 }
 
 int compute_kkt(dot_ctx* c) {
@@ -238,44 +292,17 @@ int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, con
   dot_options o;
   dot_default_options(&o);
   if (opt) o = *opt;
-  if (!(o.tau > 0.0 && o.tau < 2.0)) return fail(nullptr, DOT_EINVAL, "tau must lie in (0, 2)");
-  if (!(o.sigma0 > 0.0 && std::isfinite(o.sigma0))) return fail(nullptr, DOT_EINVAL, "sigma0 must be > 0");
-  if (!(o.s_sigma > 1.0) || !(o.s_r > 1.0)) return fail(nullptr, DOT_EINVAL, "s_sigma and s_r must be > 1");
-  if (o.check_every < 0) return fail(nullptr, DOT_EINVAL, "check_every must be >= 0");
-  if (!(o.obstacle_weight > 0.0 && std::isfinite(o.obstacle_weight)))
-    return fail(nullptr, DOT_EINVAL, "obstacle_weight must be > 0");
-  if (o.prec != DOT_FP64 && o.prec != DOT_MIXED) return fail(nullptr, DOT_EINVAL, "unknown precision");
+  if (check_options(o, &why) != DOT_OK) return fail(nullptr, DOT_EINVAL, why);
 
   std::unique_ptr<dot_ctx> c(new dot_ctx());
   c->grid = *grid;
   c->opt = o;
   c->geo = make_geo(*grid);
   const Geo& g = c->geo;
-  const long long P = g.P;
-  // densities -> cell masses (eq. (defc)), each normalised to 1
-  double s0 = 0.0, s1 = 0.0;
-  for (long long i = 0; i < P; ++i) {
-    if (!std::isfinite(rho0[i]) || !std::isfinite(rho1[i]) || rho0[i] < 0.0 || rho1[i] < 0.0)
-      return fail(nullptr, DOT_EINVAL, "densities must be finite and non-negative");
-    s0 += rho0[i];
-    s1 += rho1[i];
-  }
-  if (!(s0 > 0.0) || !(s1 > 0.0) || !std::isfinite(s0) || !std::isfinite(s1))
-    return fail(nullptr, DOT_EINVAL, "densities must have positive finite mass");
-  c->m0.resize(P);
-  c->m1.resize(P);
-  c->omega.resize(P);
   bool any_mask = false;
-  // c of eq. (defc) as cell-average densities: mass / (h_1 ... h_D) (the data scaling
-  // of Sec. 5.3; it leaves phi and q unchanged and makes alpha_0 / h_0 the density)
-  const double inv_cell = (double)P;
-  for (long long i = 0; i < P; ++i) {
-    c->m0[i] = rho0[i] / s0 * inv_cell;
-    c->m1[i] = rho1[i] / s1 * inv_cell;
-    const bool ob = mask && mask[i];
-    any_mask = any_mask || ob;
-    c->omega[i] = ob ? o.obstacle_weight : 1.0;
-  }
+  if (prepare_densities(g, rho0, rho1, mask, o.obstacle_weight, &c->m0, &c->m1, &c->omega, &any_mask, &why) !=
+      DOT_OK)
+    return fail(nullptr, DOT_EINVAL, why);
   c->stream = (cudaStream_t)stream;
   size_t need = path_workspace_bytes(g, o.prec);
   if (workspace) {

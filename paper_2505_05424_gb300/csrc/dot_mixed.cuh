@@ -4,6 +4,17 @@
 
 namespace dot {
 
+// Per-solve scalars of a batch, read by the kernels from device memory so that a
+// captured launch sequence serves every penalty value.
+struct SlotParam {
+  float2 isg;   // 1/sigma as a two-float
+  float ts;     // tau * sigma
+  int active;   // 0: the slot holds no solve; its blocks return at once
+};
+
+// A batch holds G solves of one grid.  Every per-solve field below is stored as
+// G consecutive copies (slot_view gives slot b's pointers); the DCT tables and
+// eigenvalues are shared.
 struct MxFields {
   float* q[kMaxD + 1];     // q_0: T*P; q_d: (T+1)*P padded
   float2* al[kMaxD + 1];   // two-float multipliers, same shapes as q
@@ -21,7 +32,37 @@ struct MxFields {
   const double* m1;        // P: rho1 densities
   const float* omega;      // P or nullptr
   const float* somega;     // P or nullptr: sqrt(omega/2)
+  const SlotParam* sp;     // G slot parameters
 };
+
+constexpr int kBsumStride = 1024;   // doubles per slot in bsum: partial sums, then mean(b)
+
+// Fields of slot b of a batch.
+__host__ __device__ inline MxFields slot_view(MxFields f, const Geo& g, int b) {
+  if (b == 0) return f;
+  const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P, P = g.P;
+  f.q[0] += b * n0;
+  f.al[0] += b * n0;
+  for (int d = 0; d < g.D; ++d) {
+    f.q[1 + d] += b * nn;
+    f.al[1 + d] += b * nn;
+  }
+  f.beta += b * g.K * n0;
+  if (f.z) f.z += b * g.K * n0;
+  f.phi += b * nn;
+  f.b += b * nn;
+  f.blo += b * nn;
+  f.phi1 += b * nn;
+  f.r += b * nn;
+  f.bsum += b * kBsumStride;
+  f.c0 += b * P;
+  f.c1 += b * P;
+  f.m0 += b * P;
+  f.m1 += b * P;
+  if (f.omega) f.omega += b * P;
+  if (f.somega) f.somega += b * P;
+  return f;
+}
 
 // Poisson solver of the mixed path: per-axis DCT matrices (FP32, and their
 // TF32 hi/lo split for the tensor-core GEMMs), 1D eigenvalues, scratch.
@@ -33,43 +74,61 @@ struct MxPoisson {
   const float* CThi[kMaxD + 1];   // TF32 split of C^T
   const float* CTlo[kMaxD + 1];
   const float* lam[kMaxD + 1];    // M, 1D Neumann eigenvalues
-  float* w1;                      // (T+1)*P scratch
-  float* w2;                      // (T+1)*P scratch
+  // time-axis tables for the tensor-core flow, rows padded to time_ld(g) floats:
+  // C hi, C lo, C^T hi, C^T lo (nullptr: the SIMT time pass is used)
+  const float* tpad[4];
+  float* w1;                      // poisson_scratch_elems(g) floats per solve of a batch
+  float* w2;
   int* err;                       // set by a tensor-core pass whose pipeline wait timed out
-  bool use_tc;                    // run eligible spatial passes on the tensor cores
+  bool use_tc;                    // run eligible passes on the tensor cores
 };
+
+// Row stride of the padded time axis (a multiple of 4 floats: 16-byte TMA rows).
+inline int time_ld(const Geo& g) { return (g.T + 1 + 3) / 4 * 4; }
+// Whether the whole Poisson solve runs on the tensor cores (the flow a batch of
+// several solves needs).
+bool poisson_tc_flow(const Geo& g, const MxPoisson& ps);
+// Scratch elements per solve for w1 / w2.
+size_t poisson_scratch_elems(const Geo& g);
 
 // Shared memory of the fused time-axis pass (C_t and two 64-column tiles).
 size_t tsolve_smem_bytes(const Geo& g);
 
-// src -> dst (src is preserved), FP32 in and out.
-void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
+// src -> dst (src is preserved), FP32 in and out, for G solves of grid g stored
+// one after the other (G > 1 needs poisson_tc_flow).
+void launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
                        LaunchCounter lc);
-// Refined solve of f.b (+ f.blo) into out (two-float); f.b is overwritten.
-// have_bsum: f.bsum already holds the partial sums of b (k_assemble_b writes them).
-constexpr int kBsumParts = 608;
-void launch_poisson_refined_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out,
+// Refined solve of f.b (+ f.blo) into out (two-float, slot-strided like phi) for
+// the G slots of a batch; f.b is overwritten.  have_bsum: f.bsum already holds
+// the partial sums of b (k_assemble_b writes them).
+constexpr int kBsumParts = 608;   // most partial sums per slot
+void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
                                bool have_bsum, cudaStream_t s, LaunchCounter lc);
-void launch_iterate_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, double sigma, double tau,
-                       cudaStream_t s, LaunchCounter lc);
-// Stopping-measure sums.  socp_part (nullable): per-block sums of |z - BFq - d|^2
-// written by the fused kernel; when given, they replace the z-based term.
-void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
-                   int nsocp, cudaStream_t s, LaunchCounter lc);
-void launch_assemble_b_mx(const Geo& g, const MxFields& f, double sigma, cudaStream_t s, LaunchCounter lc);
+// Lines 1-6 of Algorithm 2 for every active slot (unfused kernels; penalties from f.sp).
+void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                       LaunchCounter lc);
+// Stopping-measure sums of every active slot into out[G][R_NSLOTS].  socp_part
+// (nullable): per-block sums of |z - BFq - d|^2 written by the fused kernel,
+// nsocp per slot; when given, they replace the z-based term.
+void launch_kkt_mx(const Geo& g, int G, const MxFields& f, double* partials, double* out,
+                   const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc);
+void launch_assemble_b_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc);
 
-// Fused lines 3-6 for D = 2 (k_fused2d.cu): reads q, alpha, beta of f, writes
-// those of fn; phi, somega from f.  socp_part: fused2d_blocks(g) doubles.
+// Fused lines 3-6 for D = 2 (k_fused2d.cu) for every active slot: reads q, alpha,
+// beta of f, writes those of fn; phi, somega, sp from f.  socp_part:
+// fused2d_blocks(g) doubles per slot.
 bool fused2d_supported(const Geo& g);
 long long fused2d_blocks(const Geo& g);
-void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
-                    double* socp_part, cudaStream_t s, LaunchCounter lc);
+void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part,
+                    cudaStream_t s, LaunchCounter lc);
 // The same pass with beta staged by TMA (needs N_y even); socp_part:
-// fused2d_tma_blocks(g) doubles.  Returns false if the tensor map cannot be built.
+// fused2d_tma_blocks(g) doubles per slot.  Returns false if the tensor map cannot
+// be built.
 bool fused2d_tma_supported(const Geo& g);
 long long fused2d_tma_blocks(const Geo& g);
-bool launch_fused2d_tma(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
-                        double* socp_part, int* err, cudaStream_t s, LaunchCounter lc);
+bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part, int* err,
+                        cudaStream_t s, LaunchCounter lc);
+// KKT partial-sum scratch (doubles) per slot.
 long long kkt_partials_len_mx(const Geo& g);
 
 }  // namespace dot

@@ -45,8 +45,9 @@ constexpr size_t kOffW2 = kOffW1 + kField;
 constexpr size_t kOffTables = kOffW2 + kField;                           // (kMaxD+1) axes x 6 tables
 constexpr size_t kOffLam = kOffTables + (size_t)(kMaxD + 1) * 6 * kTable; // (kMaxD+1) axes
 constexpr size_t kOffSum = kOffLam + (size_t)(kMaxD + 1) * kLam;
-constexpr size_t kOffErr = kOffSum + 1024 * sizeof(double);  // kBsumParts partial sums, then mean(b)
-constexpr size_t kScratchBytes = kOffErr + 256;
+constexpr size_t kOffErr = kOffSum + kBsumStride * sizeof(double);  // partial sums of b, then mean(b)
+constexpr size_t kOffParam = kOffErr + 256;                            // one SlotParam (active)
+constexpr size_t kScratchBytes = kOffParam + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -128,6 +129,7 @@ extern "C" int dot_poisson_f32_noalloc(const dot_grid* grid, const float* b, flo
   ps.w2 = (float*)(base + kOffW2);
   ps.err = (int*)(base + kOffErr);
   ps.use_tc = true;
+  f.sp = (const SlotParam*)(base + kOffParam);
 
   // DCT tables of this grid (orthonormal DCT-II, its transpose and their TF32 splits)
   for (int a = 0; a <= g.D; ++a) {
@@ -171,14 +173,17 @@ extern "C" int dot_poisson_f32_noalloc(const dot_grid* grid, const float* b, flo
   }
   // the right-hand side is copied in (the solve overwrites it with the correction);
   // its low part and the error flag must start at zero
+  static const SlotParam kOne = {make_float2(0.f, 0.f), 0.f, 1};
   e = cudaMemcpyAsync(f.b, b, (size_t)nn * sizeof(float), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.blo, 0, (size_t)nn * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ps.err, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + kOffParam, &kOne, sizeof(kOne), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fail(DOT_ECUDA, "scratch set-up: ", cudaGetErrorString(e));
   long launches = 0;
   LaunchCounter lc{&launches};
-  static_assert(kBsumParts + 2 <= 1024, "scratch holds 1024 doubles of partial sums and mean");
-  launch_poisson_refined_mx(g, f, ps, reinterpret_cast<float2*>(phi), false, s, lc);
+  static_assert(kBsumParts + 2 <= kBsumStride, "the partial sums and the mean fit one slot's stride");
+  launch_poisson_refined_mx(g, 1, f, ps, reinterpret_cast<float2*>(phi), false, s, lc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DOT_ECUDA, "launch: ", cudaGetErrorString(e));
   int flag = 0;

@@ -12,6 +12,16 @@
 namespace dot {
 
 Geo make_geo(const dot_grid& gr);
+bool grid_valid(const dot_grid* g, std::string* why);
+int check_options(const dot_options& o, std::string* why);
+// Densities -> c (cell-average densities, each of mass 1) and omega; DOT_EINVAL
+// with a message for non-finite, negative or massless input.
+int prepare_densities(const Geo& g, const double* rho0, const double* rho1, const uint8_t* mask,
+                      double obstacle_weight, std::vector<double>* m0, std::vector<double>* m1,
+                      std::vector<double>* omega, bool* any_mask, std::string* why);
+// Stopping measures of Sec. 5.3 (kkt[DOT_KKT_LEN]) from the reduction slots r;
+// cn2 = sum of squares of c.
+void kkt_measures(const Geo& g, double cn2, const double* r, long iters, double sigma, double* kkt);
 
 // Bump allocator over the caller's workspace; with base == nullptr it only
 // measures (used by dot_workspace_bytes).

@@ -117,18 +117,30 @@ __device__ __forceinline__ bool ff_le(float2 a, float2 b) {
 
 __device__ __forceinline__ float ff_round(float2 a) { return a.x + a.y; }
 
-// Projection onto the second-order cone {y_0 >= |ybar|} (eq. (app-proj)) in
-// two-float arithmetic.  The input of the ALM projection is dominated by
-// -beta/sigma, often 10^2 - 10^3 times the O(1) point it projects to, so the
-// boundary case (y_0 + |ybar|)/2 cancels; two-float arithmetic keeps ~2^-44
-// relative accuracy there.  Case order: y if |ybar| <= y_0; 0 if |ybar| <= -y_0;
-// else the boundary formula.
+// Projection onto the second-order cone {y_0 >= |ybar|} (eq. (app-proj)) of a
+// two-float input.  The input of the ALM projection is dominated by -beta/sigma,
+// often 10^2 - 10^3 times the O(1) point it projects to, so the tests and the
+// boundary value (y_0 + |ybar|)/2 cancel: |ybar| and that sum are formed in
+// two-float arithmetic (~2^-44 relative).  The boundary direction ybar/|ybar| only
+// scales the O(1) result, so it is taken in FP32: every output component is then
+// within a few FP32 ulps of its own (O(1)) value, the precision it is stored in.
+// Case order: y if |ybar| <= y_0; 0 if |ybar| <= -y_0; else the boundary formula.
 template <int K>
 __device__ __forceinline__ void ff_proj_soc(float2* y) {
-  float2 nb2 = make_float2(0.f, 0.f);
+  // |ybar|^2: exact squares of the high parts summed with TwoSum, the rounding
+  // errors and the cross terms 2 hi lo collected in one FP32 correction (all
+  // terms are non-negative, so the compensated sum is accurate to ~2^-44)
+  float sh = 0.f, sc = 0.f;
 #pragma unroll
-  for (int j = 1; j < K; ++j) nb2 = ff_add(nb2, ff_sqr(y[j]));
-  const float2 nb = ff_sqrt(nb2);
+  for (int j = 1; j < K; ++j) {
+    const float h = y[j].x;
+    const float p = h * h;
+    const float e = fmaf(2.f * h, y[j].y, fmaf(h, h, -p));
+    const float2 t = two_sum(sh, p);
+    sh = t.x;
+    sc += t.y + e;
+  }
+  const float2 nb = ff_sqrt(quick_two_sum(sh, sc));
   if (ff_le(nb, y[0])) return;
   if (ff_le(nb, ff_neg(y[0]))) {
 #pragma unroll
@@ -137,10 +149,10 @@ __device__ __forceinline__ void ff_proj_soc(float2* y) {
   }
   const float2 sum = ff_add(y[0], nb);
   const float2 a = make_float2(0.5f * sum.x, 0.5f * sum.y);
-  const float2 sc = ff_div(a, nb);
+  const float scale = (a.x + a.y) / nb.x;
   y[0] = a;
 #pragma unroll
-  for (int j = 1; j < K; ++j) y[j] = ff_mul(sc, y[j]);
+  for (int j = 1; j < K; ++j) y[j] = make_float2(scale * y[j].x, 0.f);
 }
 
 }  // namespace dot

@@ -3,15 +3,22 @@
 // split precision with FP32 accumulation.
 //
 // A pass applies the M x M matrix B (the orthonormal DCT-II matrix C for a forward
-// transform, C^T for the inverse) along the innermost axis of a field stored as
-// [A][Bd][K] (K = M innermost):
-//     Out(k, a, b) = sum_j X(a, b, j) B(k, j)
-// and writes the result with the transformed axis moved outermost, so that the
-// next axis becomes the innermost one and every pass is a K-major GEMM:
-//   mode ROWS_FLAT  tile rows r = a*Bd + b (128 consecutive r); Out[k][r]
-//   mode ROWS_A     tile rows = 128 consecutive a at fixed b;   Out[b][k][a]
-// In both modes the 32 lanes of a warp hold 32 consecutive output addresses for
-// every column k, so the epilogue stores are coalesced.
+// transform, C^T for the inverse) along the innermost axis of a field whose rows
+// are K = M contiguous values (row stride ldx >= K, a multiple of 4):
+//     Out(k, row) = sum_j X(row, j) B(k, j)
+// Rows come in G groups (independent solves of one batch, stored one after the
+// other).  Output modes:
+//   ROWS_FLAT  tile rows r = 128 consecutive rows; with r = g*A + a and a = a1*M + a0,
+//              Out[g][k][a1][a0] with the a0 runs padded to stride ldo (M = 1, ldo = 1:
+//              plain Out[g][k][a]): the transformed axis moves outermost in the group
+//   ROWS_A     input [G][A][Bd][K]; tile rows = 128 consecutive a at fixed (g, b);
+//              Out[g][b][k][a]
+//   KEEP       Out[r][k] with row stride ldo, each value divided by the Neumann
+//              eigenvalue lam_0(k) + sum_d lam_d(k_d(r mod P)) (the zero mode -> 0):
+//              the time-axis forward transform and scaling of the Poisson solve
+// In ROWS_FLAT and ROWS_A the 32 lanes of a warp hold 32 consecutive output
+// addresses for every column k, so the epilogue stores are coalesced.  Columns of
+// X beyond K and rows of B beyond K are zero-filled by the TMA unit.
 //
 // 3xTF32: x = x_hi + x_lo with x_hi = tf32_rna(x) and x_lo = x - x_hi (exact in
 // FP32); B likewise (split once on the host).  Each K-step issues
@@ -89,10 +96,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int w) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
       : "memory");
 }
 
@@ -136,10 +144,18 @@ struct PassArgs {
   float* out;
   int K;           // length of the transformed axis (= reduction length)
   int Nout;        // output frequencies computed (MMA N, multiple of 16, <= 256)
-  int Kvalid;      // valid output columns written (= K)
-  int mode;        // 0 = ROWS_FLAT, 1 = ROWS_A
-  long long R;     // ROWS_FLAT: total rows
-  int A, Bd;       // ROWS_A: extents of a and b
+  int mode;        // TC_ROWS_FLAT, TC_ROWS_A, TC_KEEP
+  long long R;     // ROWS_FLAT / KEEP: total rows (all groups)
+  int A, Bd, G;    // ROWS_FLAT: rows per group A; ROWS_A: extents of a, b; G groups
+  FastDiv fA, fM;  // division by A and by M (ROWS_FLAT)
+  int M, ldo;      // ROWS_FLAT: runs of M rows, stride ldo; KEEP: output row stride
+  // KEEP: eigenvalue tables (lam[0] along the transformed axis) and the spatial
+  // decode of r mod P
+  const float* lam[kMaxD + 1];
+  int D;
+  int N[kMaxD];
+  unsigned P;
+  FastDiv fP, fS[kMaxD], fN[kMaxD];
   int* err;
 };
 
@@ -170,13 +186,15 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
   const int nchunks = (pa.K + kChunkK - 1) / kChunkK;
   // tile coordinates
   long long row0 = 0;
-  int a0 = 0, bfix = 0;
-  if (pa.mode == 0) {
+  int a0 = 0, bfix = 0, gfix = 0;
+  if (pa.mode != TC_ROWS_A) {
     row0 = (long long)blockIdx.x * kTileM;
   } else {
     const int tiles_a = (pa.A + kTileM - 1) / kTileM;
-    bfix = blockIdx.x / tiles_a;
-    a0 = (blockIdx.x % tiles_a) * kTileM;
+    const int tb = blockIdx.x / tiles_a;
+    a0 = (blockIdx.x - tb * tiles_a) * kTileM;
+    gfix = tb / pa.Bd;
+    bfix = tb - gfix * pa.Bd;
   }
 
   if (threadIdx.x == 0) {
@@ -207,8 +225,8 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
         if (c >= kStages && !mbar_wait(&empty[s], (it - 1) & 1)) { atomicExch(&s_fail, 1); break; }
         if (s_fail) break;
         mbar_expect_tx(&full[s], bytes);
-        if (pa.mode == 0) tma_load_2d(sx[s], &tm_x, &full[s], c * kChunkK, (int)row0);
-        else tma_load_3d(sx[s], &tm_x, &full[s], c * kChunkK, bfix, a0);
+        if (pa.mode != TC_ROWS_A) tma_load_2d(sx[s], &tm_x, &full[s], c * kChunkK, (int)row0);
+        else tma_load_4d(sx[s], &tm_x, &full[s], c * kChunkK, bfix, a0, gfix);
         tma_load_2d(sbh[s], &tm_bhi, &full[s], c * kChunkK, 0);
         tma_load_2d(sbl[s], &tm_blo, &full[s], c * kChunkK, 0);
       }
@@ -267,19 +285,37 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
     if (ok) {
       const int wq = warp & 3;                 // TMEM lane quarter this warp may access
       const int row = wq * 32 + lane;          // row within the tile
-      long long out_base;
-      long long col_stride;
+      long long out_base = 0, col_stride = 1;
       bool valid;
-      if (pa.mode == 0) {
+      float lsp = 0.f;        // KEEP: spatial part of the eigenvalue
+      bool zero_mode = false;
+      if (pa.mode == TC_ROWS_FLAT) {
         const long long r = row0 + row;
         valid = r < pa.R;
-        out_base = r;
-        col_stride = pa.R;
-      } else {
+        if (valid) {
+          const unsigned g = fdiv((unsigned)r, pa.fA), a = (unsigned)r - g * (unsigned)pa.A;
+          const unsigned a1 = fdiv(a, pa.fM), a0r = a - a1 * (unsigned)pa.M;
+          col_stride = (long long)(pa.A / pa.M) * pa.ldo;
+          out_base = (long long)g * pa.K * col_stride + (long long)a1 * pa.ldo + a0r;
+        }
+      } else if (pa.mode == TC_ROWS_A) {
         const int a = a0 + row;
         valid = a < pa.A;
-        out_base = (long long)bfix * pa.Kvalid * pa.A + a;
         col_stride = pa.A;
+        out_base = ((long long)gfix * pa.Bd + bfix) * pa.K * pa.A + a;
+      } else {
+        const long long r = row0 + row;
+        valid = r < pa.R;
+        if (valid) {
+          out_base = r * pa.ldo;
+          const unsigned sp = (unsigned)r - fdiv((unsigned)r, pa.fP) * pa.P;
+          zero_mode = sp == 0;
+          for (int d = 0; d < pa.D; ++d) {
+            const unsigned q = fdiv(sp, pa.fS[d]);
+            const unsigned kd = d == 0 ? q : q - fdiv(q, pa.fN[d]) * (unsigned)pa.N[d];
+            lsp += pa.lam[1 + d][kd];
+          }
+        }
       }
       for (int c0 = 0; c0 < pa.Nout; c0 += 16) {
         uint32_t v[16];
@@ -290,11 +326,29 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (valid) {
+        if (!valid) continue;
+        if (pa.mode == TC_KEEP) {
+          float w[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int k = c0 + j;
-            if (k < pa.Kvalid) pa.out[out_base + (long long)k * col_stride] = __uint_as_float(v[j]);
+            const float lam = (k < pa.K ? pa.lam[0][k] : 1.f) + lsp;
+            w[j] = (k == 0 && zero_mode) ? 0.f : __uint_as_float(v[j]) / lam;
+          }
+          float* o = pa.out + out_base + c0;
+          if (c0 + 16 <= pa.K) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < pa.K) o[j] = w[j];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int k = c0 + j;
+            if (k < pa.K) pa.out[out_base + (long long)k * col_stride] = __uint_as_float(v[j]);
           }
         }
       }
@@ -326,7 +380,7 @@ bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t* dims,
             const cuuint32_t* box) {
   auto fn = get_encode();
   if (!fn) return false;
-  cuuint32_t estr[3] = {1, 1, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void*)base, dims, strides_bytes, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -345,51 +399,70 @@ bool encode_tensor_map(CUtensorMap* m, CUtensorMapDataType type, int rank, const
   return r == CUDA_SUCCESS;
 }
 
-bool tc_pass_supported(int K) { return K >= 4 && K <= kMaxN && K % 4 == 0; }
+bool tc_pass_supported(int K) { return K >= 1 && K <= kMaxN; }
 
 int tc_smem_bytes() { return kSmemBytes; }
 
-// One pass: X viewed as [A][Bd][K] (ROWS_A) or [R][K] (ROWS_FLAT); Bhi/Blo are
-// [K][K] matrices (row k = output frequency).  Returns false if a tensor map
-// cannot be encoded (the caller reports DOT_ECUDA).
-bool launch_dct_pass_tc(const float* X, const float* Bhi, const float* Blo, float* out, int K, int mode,
-                        long long R, int A, int Bd, int* err, cudaStream_t s) {
+bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_dct_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     attr_set = true;
   }
+  const int K = p.K;
+  if (!tc_pass_supported(K) || p.ldx < K || p.ldx % 4 != 0 || p.ldb < K || p.ldb % 4 != 0) return false;
+  if (((uintptr_t)p.X & 15) || ((uintptr_t)p.Bhi & 15) || ((uintptr_t)p.Blo & 15)) return false;
   const int Nout = (K + 15) / 16 * 16;
   CUtensorMap mx, mh, ml;
   bool ok;
-  if (mode == 0) {
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)R};
-    cuuint64_t str[1] = {(cuuint64_t)K * 4};
+  if (p.mode != TC_ROWS_A) {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)p.R};
+    cuuint64_t str[1] = {(cuuint64_t)p.ldx * 4};
     cuuint32_t box[2] = {kChunkK, kTileM};
-    ok = encode(&mx, X, 2, dims, str, box);
+    ok = encode(&mx, p.X, 2, dims, str, box);
   } else {
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)Bd, (cuuint64_t)A};
-    cuuint64_t str[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * 4 * Bd};
-    cuuint32_t box[3] = {kChunkK, 1, kTileM};
-    ok = encode(&mx, X, 3, dims, str, box);
+    cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)p.Bd, (cuuint64_t)p.A, (cuuint64_t)p.G};
+    cuuint64_t str[3] = {(cuuint64_t)p.ldx * 4, (cuuint64_t)p.ldx * 4 * p.Bd,
+                         (cuuint64_t)p.ldx * 4 * p.Bd * p.A};
+    cuuint32_t box[4] = {kChunkK, 1, kTileM, 1};
+    ok = encode(&mx, p.X, 4, dims, str, box);
   }
   cuuint64_t bdims[2] = {(cuuint64_t)K, (cuuint64_t)K};
-  cuuint64_t bstr[1] = {(cuuint64_t)K * 4};
+  cuuint64_t bstr[1] = {(cuuint64_t)p.ldb * 4};
   cuuint32_t bbox[2] = {kChunkK, (cuuint32_t)Nout};
-  ok = ok && encode(&mh, Bhi, 2, bdims, bstr, bbox) && encode(&ml, Blo, 2, bdims, bstr, bbox);
+  ok = ok && encode(&mh, p.Bhi, 2, bdims, bstr, bbox) && encode(&ml, p.Blo, 2, bdims, bstr, bbox);
   if (!ok) return false;
   PassArgs pa;
-  pa.out = out;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.out = p.out;
   pa.K = K;
   pa.Nout = Nout;
-  pa.Kvalid = K;
-  pa.mode = mode;
-  pa.R = R;
-  pa.A = A;
-  pa.Bd = Bd;
-  pa.err = err;
-  unsigned grid = mode == 0 ? (unsigned)((R + kTileM - 1) / kTileM)
-                            : (unsigned)(Bd * ((A + kTileM - 1) / kTileM));
+  pa.mode = p.mode;
+  pa.R = p.R;
+  pa.A = p.A > 0 ? p.A : 1;
+  pa.Bd = p.Bd > 0 ? p.Bd : 1;
+  pa.G = p.G > 0 ? p.G : 1;
+  pa.M = p.M > 0 ? p.M : 1;
+  pa.ldo = p.ldo > 0 ? p.ldo : 1;
+  pa.fA = make_fastdiv((unsigned)pa.A);
+  pa.fM = make_fastdiv((unsigned)pa.M);
+  pa.err = p.err;
+  if (p.mode == TC_ROWS_FLAT && (p.R % pa.A != 0 || pa.A % pa.M != 0 || pa.ldo < pa.M)) return false;
+  if (p.mode == TC_KEEP) {
+    if (!p.geo || pa.ldo < K || pa.ldo % 4 != 0 || ((uintptr_t)p.out & 15)) return false;
+    const Geo& g = *p.geo;
+    pa.D = g.D;
+    for (int a = 0; a <= g.D; ++a) pa.lam[a] = p.lam[a];
+    for (int d = 0; d < kMaxD; ++d) {
+      pa.N[d] = g.N[d];
+      pa.fS[d] = g.fS[d];
+      pa.fN[d] = g.fN[d];
+    }
+    pa.P = (unsigned)g.P;
+    pa.fP = g.fP;
+  }
+  unsigned grid = p.mode != TC_ROWS_A ? (unsigned)((p.R + kTileM - 1) / kTileM)
+                                      : (unsigned)(pa.G * pa.Bd * ((p.A + kTileM - 1) / kTileM));
   k_dct_pass_tc<<<grid, kThreadsTC, kSmemBytes, s>>>(mx, mh, ml, pa);
   return true;
 }

@@ -46,12 +46,39 @@ struct FusedArgs {
   float2* betan;
   const float2* phi;   // phi^{k+1}
   const float* somega;
-  float2 isg;          // 1/sigma as a two-float
-  float ts;            // tau * sigma
-  int tchunk;
+  float2 isg;          // 1/sigma as a two-float (set per slot from sp)
+  float ts;            // tau * sigma (set per slot from sp)
+  int tchunk;          // cone times per CTA
+  int nchunk;          // time chunks per slot (grid z = slots x chunks)
+  const SlotParam* sp;
   double* socp_part;   // per-block sum of |z - B F q^{k+1} - d|^2, or nullptr
+  long long socp_per_slot;
   int* err;            // set when a pipeline wait gave up
 };
+
+// The arguments of slot b of a batch.
+__device__ __forceinline__ FusedArgs fused_slot(FusedArgs a, const Geo& g, int b) {
+  const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
+  a.isg = a.sp[b].isg;
+  a.ts = a.sp[b].ts;
+  if (b == 0) return a;
+  a.q[0] += b * n0;
+  a.al[0] += b * n0;
+  a.qn[0] += b * n0;
+  a.aln[0] += b * n0;
+  for (int d = 1; d < 3; ++d) {
+    a.q[d] += b * nn;
+    a.al[d] += b * nn;
+    a.qn[d] += b * nn;
+    a.aln[d] += b * nn;
+  }
+  a.beta += b * K2 * n0;
+  a.betan += b * K2 * n0;
+  a.phi += b * nn;
+  if (a.somega) a.somega += b * g.P;
+  if (a.socp_part) a.socp_part += b * a.socp_per_slot;
+  return a;
+}
 
 // halo-ring cone number r (0..99) -> (xh, yh) on the border of the HX x HY rectangle
 __device__ __forceinline__ void ring_pos(int r, int* xh, int* yh) {
@@ -107,7 +134,10 @@ __device__ __forceinline__ bool cone_z(const Geo& g, const FusedArgs& a, int t, 
 
 constexpr int kSmemFused = (2 * 8 * NH) * 8 + (2 * NQ1 + 2 * NQ2) * 4;
 
-__global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) {
+  const int slot = blockIdx.z / a_in.nchunk, chunk = blockIdx.z - slot * a_in.nchunk;
+  if (!a_in.sp[slot].active) return;
+  const FusedArgs a = fused_slot(a_in, g, slot);
   // u_1..u_8 (two-float) of every halo cone at two time levels, then q^{k+1} on
   // the tile's x-faces and y-faces at two node levels
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -118,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a) {
   const int tid = threadIdx.x;
   const int ly = tid & 31, lx = tid >> 5;   // owned nodes (x0 + lx + 8r, y0 + ly)
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int ta = blockIdx.z * a.tchunk;
+  const int ta = chunk * a.tchunk;
   const int tb = min(g.T, ta + a.tchunk);
   const bool last_chunk = (tb == g.T);
   const long long P = g.P, n0 = (long long)g.T * P;
@@ -321,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a) {
     if (tid == 0) {
       double b = 0.0;
       for (int w = 0; w < kThreads / 32; ++w) b += wsum[w];
-      a.socp_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+      a.socp_part[(chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
     }
   }
 }
@@ -335,8 +365,8 @@ long long fused2d_blocks(const Geo& g) {
   return (long long)((g.N[0] + TX - 1) / TX) * ((g.N[1] + TY - 1) / TY) * ((g.T + tchunk - 1) / tchunk);
 }
 
-void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
-                    double* socp_part, cudaStream_t s, LaunchCounter lc) {
+void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part,
+                    cudaStream_t s, LaunchCounter lc) {
   FusedArgs a;
   for (int d = 0; d < 3; ++d) {
     a.q[d] = f.q[d];
@@ -348,13 +378,15 @@ void launch_fused2d(const Geo& g, const MxFields& f, const MxFields& fn, double 
   a.betan = fn.beta;
   a.phi = f.phi;
   a.somega = f.somega;
-  a.isg = ff_from_double(1.0 / (double)sigma);
-  a.ts = tau * sigma;
+  a.isg = make_float2(0.f, 0.f);
+  a.ts = 0.f;
   a.tchunk = g.T <= 16 ? g.T : 16;
+  a.nchunk = (g.T + a.tchunk - 1) / a.tchunk;
+  a.sp = f.sp;
   a.socp_part = socp_part;
+  a.socp_per_slot = fused2d_blocks(g);
   a.err = nullptr;
-  dim3 grid((unsigned)((g.N[0] + TX - 1) / TX), (unsigned)((g.N[1] + TY - 1) / TY),
-            (unsigned)((g.T + a.tchunk - 1) / a.tchunk));
+  dim3 grid((unsigned)((g.N[0] + TX - 1) / TX), (unsigned)((g.N[1] + TY - 1) / TY), (unsigned)(a.nchunk * G));
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_fused2d, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFused);
@@ -412,13 +444,14 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
-__device__ __forceinline__ void issue_beta(const CUtensorMap* tm, float2* dst, uint64_t* bar, int y, int x, int t) {
+__device__ __forceinline__ void issue_beta(const CUtensorMap* tm, float2* dst, uint64_t* bar, int y, int x, int t,
+                                           int slot) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(kBetaTileBytes)
                : "memory");
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];"
-      ::"r"(sa(dst)), "l"(tm), "r"(sa(bar)), "r"(y), "r"(x), "r"(t), "r"(0)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
+      ::"r"(sa(dst)), "l"(tm), "r"(sa(bar)), "r"(y), "r"(x), "r"(t), "r"(0), "r"(slot)
       : "memory");
 }
 
@@ -457,7 +490,10 @@ __device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, co
 }
 
 __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ CUtensorMap tmb, Geo g,
-                                                        FusedArgs a) {
+                                                        FusedArgs a_in) {
+  const int slot = blockIdx.z / a_in.nchunk, chunk = blockIdx.z - slot * a_in.nchunk;
+  if (!a_in.sp[slot].active) return;
+  const FusedArgs a = fused_slot(a_in, g, slot);
   extern __shared__ __align__(128) unsigned char sm[];
   float2* btiles = reinterpret_cast<float2*>(sm);
   float (*zt)[8][VNH] = reinterpret_cast<float (*)[8][VNH]>(sm + kOffZ);
@@ -468,7 +504,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
   const int tid = threadIdx.x;
   const int ly = tid & 31, lx = tid >> 5;       // owned node (x0 + lx, y0 + ly)
   const int x0 = blockIdx.x * VX, y0 = blockIdx.y * VY;
-  const int ta = blockIdx.z * a.tchunk;
+  const int ta = chunk * a.tchunk;
   const int tb = min(g.T, ta + a.tchunk);
   const bool last_chunk = (tb == g.T);
   const int P = (int)g.P, n0 = g.T * P, N1 = g.N[1];
@@ -490,7 +526,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
   unsigned phase[3] = {0u, 0u, 0u};
   bool inflight[3] = {false, false, false};   // meaningful on the issuing thread
   if (tid == 0 && tstart <= tlast_cone) {
-    issue_beta(&tmb, btiles + (tstart % 3) * kBetaTile, &bars[tstart % 3], y0 - 2, x0 - 1, tstart);
+    issue_beta(&tmb, btiles + (tstart % 3) * kBetaTile, &bars[tstart % 3], y0 - 2, x0 - 1, tstart, slot);
     inflight[tstart % 3] = true;
   }
 
@@ -506,7 +542,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
     // prefetch the next cone time's beta into the buffer freed at the end of step t-1
     if (tid == 0 && t + 1 <= tlast_cone) {
       const int nb = (t + 1) % 3;
-      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1);
+      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1, slot);
       inflight[nb] = true;
     }
     if (t <= g.T - 1) {
@@ -686,7 +722,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
     if (tid == 0) {
       double b = 0.0;
       for (int w = 0; w < 8; ++w) b += wsum[w];
-      a.socp_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
+      a.socp_part[(chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
     }
   }
 }
@@ -703,8 +739,8 @@ long long fused2d_tma_blocks(const Geo& g) {
   return (long long)((g.N[0] + VX - 1) / VX) * ((g.N[1] + VY - 1) / VY) * ((g.T + tchunk - 1) / tchunk);
 }
 
-bool launch_fused2d_tma(const Geo& g, const MxFields& f, const MxFields& fn, double sigma, double tau,
-                        double* socp_part, int* err, cudaStream_t s, LaunchCounter lc) {
+bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part, int* err,
+                        cudaStream_t s, LaunchCounter lc) {
   FusedArgs a;
   for (int d = 0; d < 3; ++d) {
     a.q[d] = f.q[d];
@@ -716,24 +752,28 @@ bool launch_fused2d_tma(const Geo& g, const MxFields& f, const MxFields& fn, dou
   a.betan = fn.beta;
   a.phi = f.phi;
   a.somega = f.somega;
-  a.isg = ff_from_double(1.0 / sigma);
-  a.ts = (float)(tau * sigma);
+  a.isg = make_float2(0.f, 0.f);
+  a.ts = 0.f;
   a.tchunk = g.T <= 16 ? g.T : 16;
+  a.nchunk = (g.T + a.tchunk - 1) / a.tchunk;
+  a.sp = f.sp;
   a.socp_part = socp_part;
+  a.socp_per_slot = fused2d_tma_blocks(g);
   a.err = err;
-  // beta as a 4-D tensor of 8-byte elements: (y, x, t, component)
+  // beta as a 5-D tensor of 8-byte elements: (y, x, t, component, slot)
   CUtensorMap tm;
-  const cuuint64_t dims[4] = {(cuuint64_t)g.N[1], (cuuint64_t)g.N[0], (cuuint64_t)g.T, (cuuint64_t)K2};
-  const cuuint64_t str[3] = {(cuuint64_t)g.N[1] * 8, (cuuint64_t)g.P * 8, (cuuint64_t)g.T * g.P * 8};
-  const cuuint32_t box[4] = {VBW, VHX, 1, K2};
-  if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, f.beta, dims, str, box)) return false;
+  const cuuint64_t dims[5] = {(cuuint64_t)g.N[1], (cuuint64_t)g.N[0], (cuuint64_t)g.T, (cuuint64_t)K2,
+                              (cuuint64_t)G};
+  const cuuint64_t str[4] = {(cuuint64_t)g.N[1] * 8, (cuuint64_t)g.P * 8, (cuuint64_t)g.T * g.P * 8,
+                             (cuuint64_t)K2 * g.T * g.P * 8};
+  const cuuint32_t box[5] = {VBW, VHX, 1, K2, 1};
+  if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, f.beta, dims, str, box)) return false;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_fused2d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemV2);
     attr = true;
   }
-  dim3 grid((unsigned)((g.N[0] + VX - 1) / VX), (unsigned)((g.N[1] + VY - 1) / VY),
-            (unsigned)((g.T + a.tchunk - 1) / a.tchunk));
+  dim3 grid((unsigned)((g.N[0] + VX - 1) / VX), (unsigned)((g.N[1] + VY - 1) / VY), (unsigned)(a.nchunk * G));
   k_fused2d_tma<<<grid, 256, kSmemV2, s>>>(tm, g, a);
   lc.launched(KID_FUSED);
   return true;

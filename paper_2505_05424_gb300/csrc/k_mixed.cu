@@ -54,8 +54,19 @@ __device__ __forceinline__ void block_sum_ff(float2 v, double* out) {
   }
 }
 
+// Zero-mode partial sums per slot: one per block of the b-assembly.
+inline int bsum_blocks(const Geo& g) {
+  const long long nn = (long long)(g.T + 1) * g.P;
+  long long b = (nn + kThreads - 1) / kThreads;
+  return (int)(b < kBsumParts ? (b < 1 ? 1 : b) : kBsumParts);
+}
+
 template <int D>
-__global__ void k_assemble_b(Geo g, MxFields f, float2 isg) {
+__global__ void k_assemble_b(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const float2 isg = fb.sp[slot].isg;
+  const MxFields f = slot_view(fb, g, slot);
   const long long n = (long long)(g.T + 1) * g.P;
   float2 bsum = make_float2(0.f, 0.f);   // this thread's part of sum(b): the zero mode
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -103,8 +114,14 @@ __global__ void k_assemble_b(Geo g, MxFields f, float2 isg) {
 // mean from the refinement residual lets the correction solve remove that leak.
 // The iteration gets these partials from k_assemble_b; the Poisson operator entry
 // points use this kernel.
-__global__ void k_sum_b(long long n, const float* __restrict__ b, const float* __restrict__ blo,
-                        double* partials) {
+__global__ void k_sum_b(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const MxFields f = slot_view(fb, g, slot);
+  const long long n = (long long)(g.T + 1) * g.P;
+  const float* b = f.b;
+  const float* blo = f.blo;
+  double* partials = f.bsum;
   float2 acc = make_float2(0.f, 0.f);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -116,10 +133,14 @@ __global__ void k_sum_b(long long n, const float* __restrict__ b, const float* _
 // exactly in two-float arithmetic (each neighbour difference by TwoSum; 1/h^2 is
 // an integer) and mean(b) from the FP64 partial sums.
 // mean(b) from the per-block partial sums, once, as a two-float in bsum[kMeanBlocks]
-__global__ void k_mean_b(long long n, double* bsum) {
+__global__ void k_mean_b(Geo g, MxFields fb, int nparts) {
+  const int slot = blockIdx.x;
+  if (!fb.sp[slot].active) return;
+  double* bsum = slot_view(fb, g, slot).bsum;
+  const long long n = (long long)(g.T + 1) * g.P;
   __shared__ double sh[kThreads];
   double v = 0.0;
-  for (int k = threadIdx.x; k < kMeanBlocks; k += blockDim.x) v += bsum[k];
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) v += bsum[k];
   sh[threadIdx.x] = v;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -134,8 +155,11 @@ __global__ void k_mean_b(long long n, double* bsum) {
 }
 
 template <int D>
-__global__ void k_residual(Geo g, MxFields f, const double* bsum_partials) {
-  const float2 mean = reinterpret_cast<const float2*>(bsum_partials + kMeanBlocks)[0];
+__global__ void k_residual(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const MxFields f = slot_view(fb, g, slot);
+  const float2 mean = reinterpret_cast<const float2*>(f.bsum + kMeanBlocks)[0];
   const long long n = (long long)(g.T + 1) * g.P;
   const float* x = f.phi1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -166,9 +190,15 @@ __global__ void k_residual(Geo g, MxFields f, const double* bsum_partials) {
   }
 }
 
-// phi = phi1 + delta as a two-float pair.
-__global__ void k_combine(long long n, const float* __restrict__ phi1, const float* __restrict__ delta,
-                          float2* __restrict__ phi) {
+// phi = phi1 + delta as a two-float pair (out is slot-strided like phi).
+__global__ void k_combine(Geo g, MxFields fb, float2* __restrict__ out) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const long long n = (long long)(g.T + 1) * g.P;
+  const MxFields f = slot_view(fb, g, slot);
+  const float* __restrict__ phi1 = f.phi1;
+  const float* __restrict__ delta = f.b;
+  float2* __restrict__ phi = out + slot * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     phi[i] = two_sum(phi1[i], delta[i]);
@@ -194,7 +224,11 @@ __device__ __forceinline__ void gather_Fq(const Geo& g, float* const* q, long lo
 // arithmetic (ff_proj_soc); z is stored rounded to FP32 (its O(1) value loses
 // only 2^-24 relative).
 template <int D>
-__global__ void k_project(Geo g, MxFields f, float2 isg) {
+__global__ void k_project(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const float2 isg = fb.sp[slot].isg;
+  const MxFields f = slot_view(fb, g, slot);
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
   const float s_default = 0.70710678118654752f;
@@ -218,7 +252,12 @@ __global__ void k_project(Geo g, MxFields f, float2 isg) {
 // Lines 4-5 on the time faces (diagonal 3, F^*B^*u = u_{K-1} - u_0), the
 // right-hand side in two-float arithmetic (alpha/sigma and beta/sigma cancel).
 template <int D>
-__global__ void k_update_q0(Geo g, MxFields f, float2 isg, float ts) {
+__global__ void k_update_q0(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const float2 isg = fb.sp[slot].isg;
+  const float ts = fb.sp[slot].ts;
+  const MxFields f = slot_view(fb, g, slot);
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
   const float ih0 = (float)g.invh[0];
@@ -240,7 +279,12 @@ __global__ void k_update_q0(Geo g, MxFields f, float2 isg, float ts) {
 // rhs = A phi + (alpha + sum_c s_c beta_c)/sigma + sum_c s_c z_c with the
 // multiplier sum in two-float arithmetic.
 template <int D>
-__global__ void k_update_qd(Geo g, MxFields f, int d, float2 isg, float ts) {
+__global__ void k_update_qd(Geo g, MxFields fb, int d) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const float2 isg = fb.sp[slot].isg;
+  const float ts = fb.sp[slot].ts;
+  const MxFields f = slot_view(fb, g, slot);
   const long long n = (long long)(g.T + 1) * g.P;
   const long long n0 = (long long)g.T * g.P;
   const float s_default = 0.70710678118654752f;
@@ -283,7 +327,11 @@ __global__ void k_update_qd(Geo g, MxFields f, int d, float2 isg, float ts) {
 
 // Line 6: beta += tau sigma (z - B F q - d).
 template <int D>
-__global__ void k_update_beta(Geo g, MxFields f, float ts) {
+__global__ void k_update_beta(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const float ts = fb.sp[slot].ts;
+  const MxFields f = slot_view(fb, g, slot);
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
   const float s_default = 0.70710678118654752f;
@@ -310,6 +358,17 @@ __global__ void k_update_beta(Geo g, MxFields f, float ts) {
 
 constexpr int kKktBlocks = 608;
 
+__host__ __device__ inline long long kkt_partials_len_slot(const Geo& g) {
+  return (long long)(g.D + 2) * kKktBlocks * R_NSLOTS;
+}
+
+// Blocks per slot of each stopping-measure kernel (at most kKktBlocks).
+inline int kkt_blocks(const Geo& g) {
+  const long long nn = (long long)(g.T + 1) * g.P;
+  const long long b = (nn + 4 * kThreads - 1) / (4 * kThreads);
+  return (int)(b < 1 ? 1 : (b > kKktBlocks ? kKktBlocks : b));
+}
+
 __device__ __forceinline__ void block_reduce_store(const float* accf, const double* accd, double* out_row) {
   __shared__ double sh[kThreads / 32][R_NSLOTS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -327,7 +386,11 @@ __device__ __forceinline__ void block_reduce_store(const float* accf, const doub
 }
 
 template <int D>
-__global__ void k_kkt_cones(Geo g, MxFields f, double* partials, int use_z) {
+__global__ void k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const MxFields f = slot_view(fb, g, slot);
+  double* partials = partials_all + slot * kkt_partials_len_slot(g);
   constexpr int K = 4 * D + 2;
   float acc[R_NSLOTS];
   double accd[R_NSLOTS];
@@ -379,7 +442,11 @@ __global__ void k_kkt_cones(Geo g, MxFields f, double* partials, int use_z) {
 }
 
 template <int D>
-__global__ void k_kkt_faces(Geo g, MxFields f, int d, double* partials) {
+__global__ void k_kkt_faces(Geo g, MxFields fb, int d, double* partials_all) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const MxFields f = slot_view(fb, g, slot);
+  double* partials = partials_all + slot * kkt_partials_len_slot(g) + (long long)(1 + d) * kKktBlocks * R_NSLOTS;
   float acc[R_NSLOTS];
   double accd[R_NSLOTS];
   for (int k = 0; k < R_NSLOTS; ++k) { acc[k] = 0.f; accd[k] = 0.0; }
@@ -392,6 +459,7 @@ __global__ void k_kkt_faces(Geo g, MxFields f, int d, double* partials) {
   const float2* a0 = f.al[0];
   const int cbase = 1 + 4 * d;
   const float ih = (float)g.invh[1 + d];
+  float2 dual = make_float2(0.f, 0.f);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int t = plane_of(g, i);
@@ -423,17 +491,24 @@ __global__ void k_kkt_faces(Geo g, MxFields f, int d, double* partials) {
     acc[R_COMPD] += (a - gv) * (a - gv);
     acc[R_ALPHAB] += a * a;
     acc[R_G] += gv * gv;
-    if (den > 0.f) accd[R_DUALOBJ] -= 0.5 * (double)a * (double)a / (double)den;
+    // dual objective term: each ratio rounded once in FP32, the sum carried as a
+    // two-float (no FP64 division on the per-element path)
+    if (den > 0.f) dual = ff_add_f(dual, -(0.5f * a) * (a / den));
     acc[R_SOCD] += (fbb + a) * (fbb + a);
     acc[R_FBB] += fbb * fbb;
   }
+  accd[R_DUALOBJ] = ff_to_double(dual);
   block_reduce_store(acc, accd, partials + (long long)blockIdx.x * R_NSLOTS);
 }
 
 // Nodes: A^*alpha + c (in two-float arithmetic: the divergence of alpha cancels
 // against c to the level of the dual residual) and <c, phi> in FP64.
 template <int D>
-__global__ void k_kkt_nodes(Geo g, MxFields f, double* partials) {
+__global__ void k_kkt_nodes(Geo g, MxFields fb, double* partials_all) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const MxFields f = slot_view(fb, g, slot);
+  double* partials = partials_all + slot * kkt_partials_len_slot(g) + (long long)(1 + D) * kKktBlocks * R_NSLOTS;
   float acc[R_NSLOTS];
   double accd[R_NSLOTS];
   for (int k = 0; k < R_NSLOTS; ++k) { acc[k] = 0.f; accd[k] = 0.0; }
@@ -470,11 +545,22 @@ __global__ void k_kkt_nodes(Geo g, MxFields f, double* partials) {
   block_reduce_store(acc, accd, partials + (long long)blockIdx.x * R_NSLOTS);
 }
 
-__global__ void k_kkt_final(const double* partials, int rows, double* out, const double* socp_part, int nsocp) {
+// rows: kernel groups (D + 2) x kb blocks; group j's partials start at row j * kKktBlocks.
+__global__ void k_kkt_final(Geo g, const SlotParam* sp, const double* partials_all, int groups, int kb,
+                            double* out_all, const double* socp_all, int nsocp) {
+  const int slot = blockIdx.x;
+  if (!sp[slot].active) return;
+  const double* partials = partials_all + slot * kkt_partials_len_slot(g);
+  double* out = out_all + slot * R_NSLOTS;
+  const double* socp_part = socp_all ? socp_all + (long long)slot * nsocp : nullptr;
+  const int rows = groups * kb;
   __shared__ double sh[kThreads];
   for (int k = 0; k < R_NSLOTS; ++k) {
     double v = 0.0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) v += partials[(long long)r * R_NSLOTS + k];
+    for (int e = threadIdx.x; e < rows; e += blockDim.x) {
+      const int j = e / kb, r = e - j * kb;
+      v += partials[((long long)j * kKktBlocks + r) * R_NSLOTS + k];
+    }
     if (k == R_SOCP && socp_part)
       for (int r = threadIdx.x; r < nsocp; r += blockDim.x) v += socp_part[r];
     sh[threadIdx.x] = v;
@@ -491,83 +577,79 @@ __global__ void k_kkt_final(const double* partials, int rows, double* out, const
 // Line 2 with one refinement step: phi1 = P(b); r = b - A^*A phi1 (exact);
 // delta = P(r); out = phi1 + delta as a two-float pair.  Overwrites f.b with delta.
 template <int D>
-void poisson_refined_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out, bool have_bsum,
-                          cudaStream_t s, LaunchCounter lc) {
+void poisson_refined_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
+                          bool have_bsum, cudaStream_t s, LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P;
+  const int nb = bsum_blocks(g);
   if (!have_bsum) {
-    k_sum_b<<<kMeanBlocks, kThreads, 0, s>>>(nn, f.b, f.blo, f.bsum);
+    k_sum_b<<<dim3(nb, G), kThreads, 0, s>>>(g, f);
     lc.launched(KID_RESIDUAL);
   }
-  k_mean_b<<<1, kThreads, 0, s>>>(nn, f.bsum);
-  launch_poisson_mx(g, ps, f.b, f.phi1, s, lc);
-  k_residual<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, f.bsum);
+  k_mean_b<<<G, kThreads, 0, s>>>(g, f, nb);
+  launch_poisson_mx(g, G, ps, f.b, f.phi1, s, lc);
+  k_residual<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
   lc.launched(KID_RESIDUAL, 2);
-  launch_poisson_mx(g, ps, f.r, f.b, s, lc);
-  k_combine<<<grid_for(nn), kThreads, 0, s>>>(nn, f.phi1, f.b, out);
+  launch_poisson_mx(g, G, ps, f.r, f.b, s, lc);
+  k_combine<<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f, out);
   lc.launched(KID_COMBINE);
 }
 
 template <int D>
-void launch_iter_tmpl(const Geo& g, const MxFields& f, const MxPoisson& ps, double sigma, double tau,
-                      cudaStream_t s, LaunchCounter lc) {
+void launch_iter_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                      LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
-  const float2 isg = ff_from_double(1.0 / sigma);
-  const float ts = (float)(tau * sigma);
-  k_assemble_b<D><<<kMeanBlocks, kThreads, 0, s>>>(g, f, isg);                   // line 1
+  k_assemble_b<D><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);              // line 1
   lc.launched(KID_ASSEMBLE_B);
-  poisson_refined_tmpl<D>(g, f, ps, f.phi, true, s, lc);                          // line 2
-  k_project<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, isg);                      // line 3
+  poisson_refined_tmpl<D>(g, G, f, ps, f.phi, true, s, lc);                        // line 2
+  k_project<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                   // line 3
   lc.launched(KID_PROJECT);
-  k_update_q0<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, isg, ts);                 // lines 4-5
+  k_update_q0<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                 // lines 4-5
   lc.launched(KID_UPDATE_Q0);
   for (int d = 0; d < D; ++d) {
-    k_update_qd<D><<<grid_for(nn), kThreads, 0, s>>>(g, f, d, isg, ts);
+    k_update_qd<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f, d);
     lc.launched(KID_UPDATE_QD);
   }
-  k_update_beta<D><<<grid_for(n0), kThreads, 0, s>>>(g, f, (float)(tau * sigma));  // line 6
+  k_update_beta<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);               // line 6
   lc.launched(KID_UPDATE_BETA);
 }
 
 template <int D>
-void launch_kkt_tmpl(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
-                     int nsocp, cudaStream_t s, LaunchCounter lc) {
-  k_kkt_cones<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, partials, socp_part ? 0 : 1);
-  for (int d = 0; d < D; ++d)
-    k_kkt_faces<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, d, partials + (long long)(1 + d) * kKktBlocks * R_NSLOTS);
-  k_kkt_nodes<D><<<kKktBlocks, kThreads, 0, s>>>(g, f, partials + (long long)(1 + D) * kKktBlocks * R_NSLOTS);
-  k_kkt_final<<<1, kThreads, 0, s>>>(partials, (D + 2) * kKktBlocks, out, socp_part, nsocp);
+void launch_kkt_tmpl(const Geo& g, int G, const MxFields& f, double* partials, double* out,
+                     const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc) {
+  const int kb = kkt_blocks(g);
+  k_kkt_cones<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, partials, socp_part ? 0 : 1);
+  for (int d = 0; d < D; ++d) k_kkt_faces<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, d, partials);
+  k_kkt_nodes<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, partials);
+  k_kkt_final<<<G, kThreads, 0, s>>>(g, f.sp, partials, D + 2, kb, out, socp_part, nsocp);
   lc.launched(KID_KKT, D + 3);
 }
 
 }  // namespace
 
-void launch_iterate_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, double sigma, double tau,
-                       cudaStream_t s, LaunchCounter lc) {
-  if (g.D == 2) launch_iter_tmpl<2>(g, f, ps, sigma, tau, s, lc);
-  else launch_iter_tmpl<3>(g, f, ps, sigma, tau, s, lc);
+void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                       LaunchCounter lc) {
+  if (g.D == 2) launch_iter_tmpl<2>(g, G, f, ps, s, lc);
+  else launch_iter_tmpl<3>(g, G, f, ps, s, lc);
 }
 
-void launch_poisson_refined_mx(const Geo& g, const MxFields& f, const MxPoisson& ps, float2* out,
+void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
                                bool have_bsum, cudaStream_t s, LaunchCounter lc) {
-  if (g.D == 2) poisson_refined_tmpl<2>(g, f, ps, out, have_bsum, s, lc);
-  else poisson_refined_tmpl<3>(g, f, ps, out, have_bsum, s, lc);
+  if (g.D == 2) poisson_refined_tmpl<2>(g, G, f, ps, out, have_bsum, s, lc);
+  else poisson_refined_tmpl<3>(g, G, f, ps, out, have_bsum, s, lc);
 }
 
-void launch_kkt_mx(const Geo& g, const MxFields& f, double* partials, double* out, const double* socp_part,
-                   int nsocp, cudaStream_t s, LaunchCounter lc) {
-  if (g.D == 2) launch_kkt_tmpl<2>(g, f, partials, out, socp_part, nsocp, s, lc);
-  else launch_kkt_tmpl<3>(g, f, partials, out, socp_part, nsocp, s, lc);
+void launch_kkt_mx(const Geo& g, int G, const MxFields& f, double* partials, double* out,
+                   const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc) {
+  if (g.D == 2) launch_kkt_tmpl<2>(g, G, f, partials, out, socp_part, nsocp, s, lc);
+  else launch_kkt_tmpl<3>(g, G, f, partials, out, socp_part, nsocp, s, lc);
 }
 
-void launch_assemble_b_mx(const Geo& g, const MxFields& f, double sigma, cudaStream_t s, LaunchCounter lc) {
-  const long long nn = (long long)(g.T + 1) * g.P;
-  const float2 isg = ff_from_double(1.0 / sigma);
-  (void)nn;
-  if (g.D == 2) k_assemble_b<2><<<kMeanBlocks, kThreads, 0, s>>>(g, f, isg);
-  else k_assemble_b<3><<<kMeanBlocks, kThreads, 0, s>>>(g, f, isg);
+void launch_assemble_b_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc) {
+  if (g.D == 2) k_assemble_b<2><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);
+  else k_assemble_b<3><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);
   lc.launched(KID_ASSEMBLE_B);
 }
 
-long long kkt_partials_len_mx(const Geo& g) { return (long long)(g.D + 2) * kKktBlocks * R_NSLOTS; }
+long long kkt_partials_len_mx(const Geo& g) { return kkt_partials_len_slot(g); }
 
 }  // namespace dot

@@ -4,14 +4,20 @@
 //
 // Data flow ("rotated" passes): every spatial pass transforms the innermost axis
 // of its input and writes that axis outermost, so every pass is a K-major GEMM:
-//   2D  [t][x][y] -y-> [ky][t][x] -x-> [kx][ky][t] -t-solve-> [t][kx][ky]
+//   2D  [t][x][y] -y-> [ky][t][x] -x-> [kx][ky][t] -t-> [t][kx][ky]
 //       -ky^T-> [y][t][kx] -kx^T (rows along y)-> [t][x][y]
-//   3D  [t][x][y][z] -z-> -y-> -x-> [kx][ky][kz][t] -t-solve-> [t][kx][ky][kz]
+//   3D  [t][x][y][z] -z-> -y-> -x-> [kx][ky][kz][t] -t-> [t][kx][ky][kz]
 //       -kz^T-> -ky^T-> [y][z][t][kx] -kx^T (rows along (y,z))-> [t][x][y][z]
-// Spatial passes run on the tensor cores (k_dct_tc.cu, 3xTF32) when the axis
-// length allows a TMA tile, otherwise on the SIMT kernel below, which computes the
-// same pass in FP32 with the same output layout.  The time axis (length T+1) is
-// one fused pass per column of spatial frequencies: DCT-II, scale, DCT-III.
+// Tensor-core flow (every axis on tcgen05, k_dct_tc.cu, 3xTF32): the last forward
+// spatial pass writes the time rows padded to ldt = 4*ceil((T+1)/4) floats, the
+// time axis runs as two passes (DCT-II with the eigenvalue scaling in its
+// epilogue, then DCT-III), and a batch of G solves of one grid is transformed in
+// the same passes (the group index is carried outermost through every layout).
+// SIMT flow (one solve; axes the tensor-core pass cannot take): the spatial passes
+// run on the kernel below, in FP32 with the same output layouts, and the time axis
+// is one fused pass per column of spatial frequencies: DCT-II, scale, DCT-III.
+#include <cstring>
+
 #include "dot_mixed.cuh"
 #include "dot_tc.cuh"
 
@@ -187,16 +193,38 @@ __global__ void __launch_bounds__(256) k_tsolve_f32(Geo g, const float* __restri
   }
 }
 
-// One spatial pass of length K over total elements n: tensor cores when possible.
+// One spatial pass of length K over total elements n (one solve): tensor cores
+// when possible, else the SIMT kernel.
 void spatial_pass(const MxPoisson& ps, int axis, bool inverse, const float* X, float* Y, int K, long long n,
                   int mode, int A, int Bd, cudaStream_t s, LaunchCounter lc) {
   const long long R = n / K;
-  const float* Bhi = inverse ? ps.CThi[axis] : ps.Chi[axis];
-  const float* Blo = inverse ? ps.CTlo[axis] : ps.Clo[axis];
-  if (ps.use_tc && tc_pass_supported(K) &&
-      launch_dct_pass_tc(X, Bhi, Blo, Y, K, mode, R, A, Bd, ps.err, s)) {
-    lc.launched(KID_DCT_TC);
-    return;
+  if (ps.use_tc && K % 4 == 0 && tc_pass_supported(K)) {
+    TcPass p;
+    std::memset(&p, 0, sizeof(p));
+    p.X = X;
+    p.ldx = K;
+    p.Bhi = inverse ? ps.CThi[axis] : ps.Chi[axis];
+    p.Blo = inverse ? ps.CTlo[axis] : ps.Clo[axis];
+    p.ldb = K;
+    p.out = Y;
+    p.K = K;
+    p.err = ps.err;
+    if (mode == 0) {
+      p.mode = TC_ROWS_FLAT;
+      p.R = R;
+      p.A = (int)R;
+      p.M = 1;
+      p.ldo = 1;
+    } else {
+      p.mode = TC_ROWS_A;
+      p.A = A;
+      p.Bd = Bd;
+      p.G = 1;
+    }
+    if (launch_tc_pass(p, s)) {
+      lc.launched(KID_DCT_TC);
+      return;
+    }
   }
   const float* Bm = inverse ? ps.CT[axis] : ps.C[axis];
   dim3 grid((unsigned)((R + kBN - 1) / kBN), (unsigned)((K + kBM - 1) / kBM));
@@ -238,14 +266,135 @@ void launch_tsolve(const Geo& g, const MxPoisson& ps, const float* X, float* Y, 
   }
 }
 
-void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
+// The tensor-core flow applies when every axis fits one tcgen05 tile and the
+// spatial rows have 16-byte strides.
+bool poisson_tc_flow(const Geo& g, const MxPoisson& ps) {
+  if (!ps.use_tc || !ps.tpad[0] || g.T + 1 > 256) return false;
+  for (int d = 0; d < g.D; ++d)
+    if (g.N[d] > 256 || g.N[d] % 4 != 0) return false;
+  return true;
+}
+
+size_t poisson_scratch_elems(const Geo& g) {
+  const size_t nn = (size_t)(g.T + 1) * g.P;
+  const size_t padded = (size_t)g.P * time_ld(g);
+  return nn > padded ? nn : padded;
+}
+
+namespace {
+
+bool tc_pass(const MxPoisson& ps, TcPass p, int axis, bool inverse, cudaStream_t s, LaunchCounter lc) {
+  p.Bhi = inverse ? ps.CThi[axis] : ps.Chi[axis];
+  p.Blo = inverse ? ps.CTlo[axis] : ps.Clo[axis];
+  p.ldb = p.K;
+  p.err = ps.err;
+  if (!launch_tc_pass(p, s)) return false;
+  lc.launched(KID_DCT_TC);
+  return true;
+}
+
+// The tensor-core flow for G solves stored one after the other.
+bool poisson_tc(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
+                LaunchCounter lc) {
+  const long long nn = (long long)(g.T + 1) * g.P;
+  const int M = g.T + 1, ldt = time_ld(g);
+  float* w[2] = {ps.w1, ps.w2};
+  const float* cur = src;
+  int nx = 0;
+  // forward spatial passes, innermost axis first; the last one (axis 1) pads the time rows
+  for (int a = g.D; a >= 1; --a) {
+    TcPass p;
+    std::memset(&p, 0, sizeof(p));
+    const int K = g.N[a - 1];
+    p.X = cur;
+    p.ldx = K;
+    p.out = w[nx];
+    p.K = K;
+    p.mode = TC_ROWS_FLAT;
+    p.R = (long long)G * nn / K;
+    p.A = (int)(nn / K);
+    p.M = a == 1 ? M : 1;
+    p.ldo = a == 1 ? ldt : 1;
+    if (!tc_pass(ps, p, a, false, s, lc)) return false;
+    cur = w[nx];
+    nx ^= 1;
+  }
+  // time axis: DCT-II + eigenvalue scale (rows keep their place), then DCT-III
+  {
+    TcPass p;
+    std::memset(&p, 0, sizeof(p));
+    p.X = cur;
+    p.ldx = ldt;
+    p.Bhi = ps.tpad[0];
+    p.Blo = ps.tpad[1];
+    p.ldb = ldt;
+    p.out = w[nx];
+    p.K = M;
+    p.mode = TC_KEEP;
+    p.R = (long long)G * g.P;
+    p.ldo = ldt;
+    p.geo = &g;
+    for (int a = 0; a <= g.D; ++a) p.lam[a] = ps.lam[a];
+    p.err = ps.err;
+    if (!launch_tc_pass(p, s)) return false;
+    lc.launched(KID_SCALE);
+    cur = w[nx];
+    nx ^= 1;
+    p.X = cur;
+    p.Bhi = ps.tpad[2];
+    p.Blo = ps.tpad[3];
+    p.out = w[nx];
+    p.mode = TC_ROWS_FLAT;
+    p.A = (int)g.P;
+    p.M = 1;
+    p.ldo = 1;
+    p.geo = nullptr;
+    if (!launch_tc_pass(p, s)) return false;
+    lc.launched(KID_SCALE);
+    cur = w[nx];
+    nx ^= 1;
+  }
+  // inverse spatial passes, innermost axis first; the last one (axis 1) runs with
+  // rows along the flattened trailing spatial axes so it lands in [t][x][...]
+  for (int a = g.D; a >= 1; --a) {
+    const bool last = (a == 1);
+    const int K = g.N[a - 1];
+    TcPass p;
+    std::memset(&p, 0, sizeof(p));
+    p.X = cur;
+    p.ldx = K;
+    p.out = last ? dst : w[nx];
+    p.K = K;
+    if (!last) {
+      p.mode = TC_ROWS_FLAT;
+      p.R = (long long)G * nn / K;
+      p.A = (int)(nn / K);
+      p.M = 1;
+      p.ldo = 1;
+    } else {
+      p.mode = TC_ROWS_A;
+      p.A = (int)(g.P / K);
+      p.Bd = M;
+      p.G = G;
+    }
+    if (!tc_pass(ps, p, a, true, s, lc)) return false;
+    cur = p.out;
+    nx ^= 1;
+  }
+  return true;
+}
+
+}  // namespace
+
+void launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
                        LaunchCounter lc) {
+  if (poisson_tc_flow(g, ps) && poisson_tc(g, G, ps, src, dst, s, lc)) return;
+  // SIMT flow (one solve)
   const long long n = (long long)(g.T + 1) * g.P;
   float* w[2] = {ps.w1, ps.w2};
   int ci = -1;   // index of the buffer holding the current field, -1 = src
   auto cur = [&]() -> const float* { return ci < 0 ? src : w[ci]; };
   auto next = [&]() { return ci < 0 ? 0 : 1 - ci; };
-  // forward spatial passes, innermost axis first
   for (int a = g.D; a >= 1; --a) {
     const int nx = next();
     spatial_pass(ps, a, false, cur(), w[nx], g.N[a - 1], n, 0, 0, 0, s, lc);
@@ -257,8 +406,6 @@ void launch_poisson_mx(const Geo& g, const MxPoisson& ps, const float* src, floa
     lc.launched(KID_SCALE);
     ci = nx;
   }
-  // inverse spatial passes, innermost axis first; the last one (axis 1) runs with
-  // rows along the flattened trailing spatial axes so it lands in [t][x][...]
   for (int a = g.D; a >= 1; --a) {
     const bool last = (a == 1);
     float* out = last ? dst : w[next()];

@@ -215,3 +215,120 @@ def dot_poisson_f32_noalloc(D: int, T: int, N_, b, phi, stream=None) -> None:
                                      ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(s))
     if rc != N.DOT_OK:
         raise DotError(rc, lib.dot_noalloc_last_error().decode())
+
+
+class DotServer:
+    """Binding of the dot_server_* functions (see include/dot.h): many DOT solves
+    of mixed grids advanced together on the current CUDA device.
+
+    submit() returns a request id; wait() blocks until it finished; result()
+    returns (objective, kkt dict, times (submit, admit, done) in seconds since the
+    server started, and rho/m/phi when the request kept its fields)."""
+
+    STATS = ("queued", "running", "finished", "batches", "bytes", "graph_launches", "kernel_launches",
+             "peak_running", "peak_batches")
+
+    def __init__(self, hbm_budget: int = 0, max_slots: int = 64, target_nodes: int = 4194304,
+                 use_graphs: bool = True, idle_ms: int = 200, **options):
+        import torch  # the device only
+        if not torch.cuda.is_available():
+            raise RuntimeError("DotServer needs a CUDA device (no CPU fallback)")
+        torch.cuda.init()
+        self.lib = N.load()
+        self.opt = default_options("mixed", **options)
+        so = N.DotServerOptions()
+        self.lib.dot_server_default_options(ctypes.byref(so))
+        so.hbm_budget = int(hbm_budget)
+        so.max_slots = int(max_slots)
+        so.target_nodes = int(target_nodes)
+        so.use_graphs = int(bool(use_graphs))
+        so.idle_ms = int(idle_ms)
+        srv = ctypes.c_void_p()
+        rc = self.lib.dot_server_create(ctypes.byref(self.opt), ctypes.byref(so), ctypes.byref(srv))
+        if rc != N.DOT_OK:
+            raise DotError(rc, self.lib.dot_server_last_error(None).decode())
+        self.srv = srv
+        self._shapes = {}
+
+    def _check(self, rc: int, allow=(N.DOT_OK,)):
+        if rc not in allow:
+            raise DotError(rc, self.lib.dot_server_last_error(self.srv).decode())
+        return rc
+
+    def submit(self, D: int, T: int, N_, rho0, rho1, mask=None, tol: float = 1e-6, maxit: int = 100000,
+               keep_fields: bool = True) -> int:
+        Ns = tuple([int(N_)] * D if np.isscalar(N_) else [int(n) for n in N_])
+        g = make_grid(D, T, Ns)
+        r0, r1 = _f64(rho0).reshape(-1), _f64(rho1).reshape(-1)
+        P = int(np.prod(Ns))
+        if r0.size != P or r1.size != P:
+            raise DotError(N.DOT_EINVAL, f"densities must have {P} entries")
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
+            if m.size != P:
+                raise DotError(N.DOT_EINVAL, "mask size mismatch")
+        rid = ctypes.c_longlong(0)
+        self._check(self.lib.dot_server_submit(
+            self.srv, ctypes.byref(g), _dp(r0), _dp(r1),
+            None if m is None else m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+            float(tol), int(maxit), int(bool(keep_fields)), ctypes.byref(rid)))
+        self._shapes[rid.value] = (int(D), int(T), Ns, bool(keep_fields))
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = -1.0):
+        """The solve status (as dot_solve returns it), or None on timeout."""
+        st = ctypes.c_int(0)
+        rc = self.lib.dot_server_wait(self.srv, int(rid), float(timeout), ctypes.byref(st))
+        if rc == N.DOT_ETIMEOUT:
+            return None
+        self._check(rc)
+        return st.value
+
+    def result(self, rid: int) -> dict:
+        if rid not in self._shapes:
+            raise DotError(N.DOT_EINVAL, f"unknown request id {rid}")
+        D, T, Ns, keep = self._shapes[rid]
+        obj = ctypes.c_double(0.0)
+        kk = np.zeros(N.DOT_KKT_LEN)
+        times = np.zeros(3)
+        out = {}
+        if keep:
+            rho = np.zeros((T,) + Ns)
+            nm = sum((T + 1) * int(np.prod(Ns)) // Ns[d] * (Ns[d] - 1) for d in range(D))
+            m = np.zeros(nm)
+            phi = np.zeros((T + 1,) + Ns)
+            self._check(self.lib.dot_server_result(self.srv, int(rid), _dp(rho), _dp(m), _dp(phi),
+                                                   ctypes.byref(obj), _dp(kk), _dp(times)))
+            out.update(rho=rho, m=m, phi=phi)
+        else:
+            self._check(self.lib.dot_server_result(self.srv, int(rid), None, None, None, ctypes.byref(obj),
+                                                   _dp(kk), _dp(times)))
+        out.update(objective=obj.value, kkt=dict(zip(N.KKT_NAMES, kk.tolist())), times=tuple(times.tolist()))
+        return out
+
+    def release(self, rid: int):
+        self._check(self.lib.dot_server_release(self.srv, int(rid)))
+        self._shapes.pop(rid, None)
+
+    def stats(self) -> dict:
+        out = np.zeros(len(self.STATS))
+        k = self.lib.dot_server_stats(self.srv, _dp(out), len(self.STATS))
+        return dict(zip(self.STATS[:k], out[:k].tolist()))
+
+    def close(self):
+        if getattr(self, "srv", None) is not None and self.srv.value:
+            self.lib.dot_server_destroy(self.srv)
+            self.srv = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -58,6 +58,23 @@ def test_refined_poisson(D, T, N):
     gpu.close()
 
 
+@pytest.mark.parametrize("D,T,N", [(2, 5, [32, 36]), (2, 64, [128, 128]), (3, 3, [8, 12, 16])])
+def test_poisson_runs_entirely_on_tensor_cores(D, T, N):
+    """Every axis fits a tcgen05 tile: each of the two solves of a refined Poisson
+    solve is D spatial passes each way plus two time passes, none on the SIMT
+    fallback."""
+    rng = np.random.default_rng(700 + T)
+    r0 = rng.random(int(np.prod(N))) + 0.1
+    _, _, gpu = pair(D, T, N, r0, r0, prec="mixed")
+    gpu.dot_profile(True)
+    gpu.dot_poisson(rng.standard_normal((T + 1) * int(np.prod(N))))
+    prof = gpu.dot_profile_read()
+    gpu.close()
+    assert prof["dct_axis"][1] == 0
+    assert prof["dct_tcgen05"][1] == 2 * 2 * D
+    assert prof["dct_scale"][1] == 2 * 2
+
+
 @pytest.mark.parametrize("D,T,N", GRIDS)
 @pytest.mark.parametrize("masked", [False, True])
 def test_one_iteration_from_random_state(D, T, N, masked):
