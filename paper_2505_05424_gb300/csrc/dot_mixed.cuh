@@ -104,6 +104,11 @@ void launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* sr
 constexpr int kBsumParts = 608;   // most partial sums per slot
 void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
                                bool have_bsum, cudaStream_t s, LaunchCounter lc);
+// Line 2 of an iteration, warm-started from the current phi (two-float): one FP32
+// solve of the exact residual b - mean(b) - A^*A phi, added to phi.  Needs the
+// partial sums of b from k_assemble_b; uses f.r and f.phi1 as scratch.
+void launch_poisson_increment_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                                 LaunchCounter lc);
 // Lines 1-6 of Algorithm 2 for every active slot (unfused kernels; penalties from f.sp).
 void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
                        LaunchCounter lc);

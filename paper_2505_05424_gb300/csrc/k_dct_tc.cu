@@ -51,9 +51,16 @@ constexpr int kThreadsTC = 192;
 constexpr unsigned kSpinLimit = 1u << 25;   // bounded mbarrier waits (well under a second of polling)
 
 constexpr int kXBytes = kTileM * kChunkK * 4;      // 16 KB
-constexpr int kBBytes = kMaxN * kChunkK * 4;       // 32 KB (one of hi/lo)
-constexpr int kStageBytes = 2 * kXBytes + 2 * kBBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+// A stage holds the X tile (hi and lo) and Nout rows of the table (hi and lo);
+// shared memory and TMEM columns are sized to Nout so that short axes run two or
+// more CTAs per SM.
+__host__ __device__ constexpr int stage_bytes(int nout) { return 2 * kXBytes + 2 * nout * kChunkK * 4; }
+__host__ __device__ constexpr int smem_bytes(int nout) { return kStages * stage_bytes(nout) + 1024 + 256; }
+constexpr int kSmemBytes = smem_bytes(kMaxN);
+// TMEM allocation: a power of two >= 32 columns
+__host__ __device__ constexpr int tmem_cols(int nout) {
+  return nout <= 32 ? 32 : nout <= 64 ? 64 : nout <= 128 ? 128 : 256;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -169,12 +176,13 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
   uint8_t* sbh[kStages];
   uint8_t* sbl[kStages];
   for (int s = 0; s < kStages; ++s) {
-    sx[s] = smem + s * kStageBytes;
+    sx[s] = smem + s * stage_bytes(pa.Nout);
     sxlo[s] = sx[s] + kXBytes;
     sbh[s] = sxlo[s] + kXBytes;
-    sbl[s] = sbh[s] + kBBytes;
+    sbl[s] = sbh[s] + pa.Nout * kChunkK * 4;
   }
-  uint64_t* bars = (uint64_t*)(smem + kStages * kStageBytes);
+  uint64_t* bars = (uint64_t*)(smem + kStages * stage_bytes(pa.Nout));
+  const uint32_t ncols = (uint32_t)tmem_cols(pa.Nout);
   uint64_t* full = bars;                 // TMA landed
   uint64_t* conv = bars + kStages;       // hi/lo split done
   uint64_t* empty = bars + 2 * kStages;  // MMAs of the stage done
@@ -209,7 +217,7 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kMaxN));
+                 "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -358,7 +366,7 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMaxN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
   }
   if (threadIdx.x == 0 && s_fail) atomicExch(pa.err, 1);
 }
@@ -463,7 +471,7 @@ bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
   }
   unsigned grid = p.mode != TC_ROWS_A ? (unsigned)((p.R + kTileM - 1) / kTileM)
                                       : (unsigned)(pa.G * pa.Bd * ((p.A + kTileM - 1) / kTileM));
-  k_dct_pass_tc<<<grid, kThreadsTC, kSmemBytes, s>>>(mx, mh, ml, pa);
+  k_dct_pass_tc<<<grid, kThreadsTC, smem_bytes(Nout), s>>>(mx, mh, ml, pa);
   return true;
 }
 

@@ -190,6 +190,65 @@ __global__ void k_residual(Geo g, MxFields fb) {
   }
 }
 
+// Line 2 warm-started from the previous iteration's potential:
+//   r = b - mean(b) - A^*A phi^k,  delta = P(r),  phi^{k+1} = phi^k + delta.
+// A^*A phi^k is accumulated from exact two-float neighbour differences of the
+// two-float phi^k, so r is exact up to its final rounding to FP32 and the new
+// potential carries the FP32 solve's relative error times |phi^{k+1} - phi^k|
+// only (the inexact subproblem solves Algorithm 1 admits; phi^0 = 0 makes the
+// first step a plain solve).
+__device__ __forceinline__ float2 ff_diff(float2 a, float2 b) {
+  const float2 d = two_sum(a.x, -b.x);
+  return make_float2(d.x, d.y + (a.y - b.y));
+}
+
+template <int D>
+__global__ void k_residual_phi(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const MxFields f = slot_view(fb, g, slot);
+  const float2 mean = reinterpret_cast<const float2*>(f.bsum + kMeanBlocks)[0];
+  const long long n = (long long)(g.T + 1) * g.P;
+  const float2* x = f.phi;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int t = plane_of(g, i);
+    const long long p = i - (long long)t * g.P;
+    const float2 xi = x[i];
+    float2 acc = make_float2(0.f, 0.f);
+    {
+      float2 s = make_float2(0.f, 0.f);
+      if (t >= 1) s = ff_add(s, ff_diff(xi, x[i - g.P]));
+      if (t < g.T) s = ff_add(s, ff_diff(xi, x[i + g.P]));
+      const float ih = (float)g.invh[0];
+      acc = ff_add(acc, ff_mul_f(s, ih * ih));
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int xd = coord(g, p, d);
+      const long long st = g.sst[d];
+      float2 s = make_float2(0.f, 0.f);
+      if (xd >= 1) s = ff_add(s, ff_diff(xi, x[i - st]));
+      if (xd <= g.N[d] - 2) s = ff_add(s, ff_diff(xi, x[i + st]));
+      const float ih = (float)g.invh[1 + d];
+      acc = ff_add(acc, ff_mul_f(s, ih * ih));
+    }
+    const float2 r = ff_add(make_float2(f.b[i], f.blo[i]), ff_neg(ff_add(acc, mean)));
+    f.r[i] = r.x + r.y;
+  }
+}
+
+// phi^{k+1} = phi^k + delta (delta in phi1).
+__global__ void k_phi_add(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  if (!fb.sp[slot].active) return;
+  const long long n = (long long)(g.T + 1) * g.P;
+  const MxFields f = slot_view(fb, g, slot);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    f.phi[i] = ff_add_f(f.phi[i], f.phi1[i]);
+}
+
 // phi = phi1 + delta as a two-float pair (out is slot-strided like phi).
 __global__ void k_combine(Geo g, MxFields fb, float2* __restrict__ out) {
   const int slot = blockIdx.y;
@@ -594,13 +653,27 @@ void poisson_refined_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisso
   lc.launched(KID_COMBINE);
 }
 
+// Line 2 for an iteration: the warm-started solve above (the partial sums of b
+// come from k_assemble_b).
+template <int D>
+void poisson_increment_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                            LaunchCounter lc) {
+  const long long nn = (long long)(g.T + 1) * g.P;
+  k_mean_b<<<G, kThreads, 0, s>>>(g, f, bsum_blocks(g));
+  k_residual_phi<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
+  lc.launched(KID_RESIDUAL, 2);
+  launch_poisson_mx(g, G, ps, f.r, f.phi1, s, lc);
+  k_phi_add<<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
+  lc.launched(KID_COMBINE);
+}
+
 template <int D>
 void launch_iter_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
                       LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
   k_assemble_b<D><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);              // line 1
   lc.launched(KID_ASSEMBLE_B);
-  poisson_refined_tmpl<D>(g, G, f, ps, f.phi, true, s, lc);                        // line 2
+  poisson_increment_tmpl<D>(g, G, f, ps, s, lc);                                   // line 2
   k_project<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                   // line 3
   lc.launched(KID_PROJECT);
   k_update_q0<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                 // lines 4-5
@@ -636,6 +709,12 @@ void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxP
                                bool have_bsum, cudaStream_t s, LaunchCounter lc) {
   if (g.D == 2) poisson_refined_tmpl<2>(g, G, f, ps, out, have_bsum, s, lc);
   else poisson_refined_tmpl<3>(g, G, f, ps, out, have_bsum, s, lc);
+}
+
+void launch_poisson_increment_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                                 LaunchCounter lc) {
+  if (g.D == 2) poisson_increment_tmpl<2>(g, G, f, ps, s, lc);
+  else poisson_increment_tmpl<3>(g, G, f, ps, s, lc);
 }
 
 void launch_kkt_mx(const Geo& g, int G, const MxFields& f, double* partials, double* out,
