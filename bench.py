@@ -38,8 +38,9 @@ WORKLOAD_DESCS = {
     "mix3d64": ("3D DOT 64^3 cells x 32 time steps, seeded mixtures of 2-4 anisotropic Gaussians "
                 "(sigma U[0.05,0.15]^3), floor 1e-4"),
     "gauss32": "2D DOT 32x32 cells x 16 time steps, Gaussians sigma 0.1 at (0.3,0.3), (0.7,0.7) + floor 1e-3",
+    "mix1024": ("2D DOT 1024x1024 cells x 32 time steps (the scalability case), seeded mixtures as mix256"),
 }
-WORKLOAD_SEEDS = {"mix256": 1002, "obst128": 1003, "mix3d64": 1004, "gauss32": None}
+WORKLOAD_SEEDS = {"mix256": 1002, "obst128": 1003, "mix3d64": 1004, "gauss32": None, "mix1024": 1005}
 # Iterations the FP64 recurrence (GPU FP64 path == oracle, lock-step tested) needs to reach
 # eta_dot <= 1e-6 on the seed-1002 instance of this workload; converts the oracle's
 # seconds per iteration into solves/s in the reference arm.  Measured by this script's
@@ -60,12 +61,16 @@ def parse():
     ap.add_argument("--fp64-maxit", type=int, default=40000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64", "mix1024"])
     ap.add_argument("--serve", type=int, default=0,
                     help="serve the first SERVE requests of the seeded serving stream (2D grids "
                          "{32^2x16, 64^2x32, 128^2x32, 256^2x64}, Poisson arrivals, 20%% masked) through "
                          "the continuous-batching server and print its JSON line instead")
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the serving stream")
+    ap.add_argument("--multilevel", type=int, default=0,
+                    help="solve every timed instance with the multilevel strategy over this many coarse levels")
+    ap.add_argument("--coarse-tol", type=float, default=0.0,
+                    help="tolerance of the coarse levels (0: the paper's max(tol*10^-v, 1e-6))")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="run this many iterations of one solve (no stopping checks) and exit: a short, "
                          "fixed launch sequence for ncu; prints no JSON")
@@ -263,9 +268,14 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     lat, iters, etas, objs = [], [], [], []
     ev0.record(stream)
+    level_iters = []
     for s in solvers:
         t0 = time.perf_counter()
-        rc = s.dot_solve(args.tol, args.maxit)
+        if args.multilevel > 0:
+            rc, its = s.dot_solve_multilevel(args.multilevel, args.tol, args.maxit, args.coarse_tol)
+            level_iters.append(its)
+        else:
+            rc = s.dot_solve(args.tol, args.maxit)
         lat.append((time.perf_counter() - t0) * 1e3)
         kk = s.dot_kkt()
         iters.append(int(kk["iterations"]))
@@ -351,6 +361,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (per-solve state > 129 MB)", "seeds": f"{base_seed}+step",
                    "parallelism": f"replicas{world}"},
         "iterations": iters, "eta_dot": etas, "objective": objs,
+        "multilevel": ({"levels": args.multilevel, "coarse_tol": args.coarse_tol or "paper",
+                        "iterations_per_level_finest_first": level_iters}
+                       if args.multilevel > 0 else None),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "it_per_s": round(sum(iters) / (elapsed_ms / 1e3), 1),
         "clocks": clk, "gpu_launches": int(gpu_launches),

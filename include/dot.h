@@ -182,6 +182,35 @@ const char *dot_last_error(const dot_ctx *ctx);
 const char *dot_version(void);
 long dot_launch_count(const dot_ctx *ctx);
 
+/* ---- Multilevel initialisation (Sec. 5, the "multilevel strategy") ----------
+ *
+ * dot_solve_multilevel solves the context's problem on grids coarsened by 2^v in
+ * time and in every spatial axis, v = levels, ..., 1 (densities averaged over
+ * 2^D-cell blocks, a block is an obstacle if any of its cells is), each level to
+ * coarse_tol, or for coarse_tol <= 0 to the paper's max(tol * 10^-v, 1e-6),
+ * starting every finer level -- and finally the context
+ * itself, solved to tol -- from the coarser solution interpolated by
+ * dot_prolong_state.  The context's state, sigma and iteration count are those of
+ * a dot_set_state followed by dot_solve.  Coarse levels use temporary contexts of
+ * the same precision and options on the same stream (their workspaces are
+ * allocated with cudaMalloc and freed before the call returns).
+ *   levels: 0..8; T and every N_d divisible by 2^levels, N_d / 2^levels >= 2.
+ *   iters (nullable): levels + 1 entries, iters[v] = iterations on level v
+ *   (iters[0] = the context's).
+ * Returns dot_solve's status for the finest level, or an error.
+ *
+ * dot_prolong_state interpolates a state (q, alpha, beta in the host layouts of
+ * dot_get_state) from grid gc to a grid gf of the same D with T and N_d at least
+ * gc's: multilinear interpolation on each field's staggered sample positions
+ * (time faces at (k + 1/2)/T and cell centres; space faces at time nodes k/T and
+ * face positions j/N_d, with zero flux at the walls), constant beyond the
+ * outermost centres; alpha and beta are scaled by gc.T / gf.T (they scale like
+ * h_0).  Host only (no device work); any pointer pair may be NULL. */
+int dot_solve_multilevel(dot_ctx *ctx, int levels, double tol, double coarse_tol, long maxit, long *iters);
+int dot_prolong_state(const dot_grid *gc, const dot_grid *gf, const double *qc, const double *alc,
+                      const double *betac, double *qf, double *alf, double *betaf);
+const char *dot_multilevel_last_error(void);
+
 /* ---- Serving: many solves advanced together (continuous batching) -----------
  *
  * The paper solves one problem at a time; this layer runs Algorithm 2 for many
@@ -198,8 +227,8 @@ long dot_launch_count(const dot_ctx *ctx);
  * kernels as a dot_create/dot_solve context of precision DOT_MIXED, so a
  * request's result does not depend on which other requests share its batch.
  *
- * Grids: D = 2 with every axis (T+1 and each N_d) at most 256 and N_d a
- * multiple of 4 are batched; other grids get batches of one slot.
+ * Grids: D = 2 with every N_d a multiple of 4 (and at most 4096) are batched;
+ * other grids get batches of one slot.
  * Threading: every function may be called from any thread. */
 typedef struct dot_server dot_server;
 

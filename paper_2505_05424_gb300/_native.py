@@ -99,7 +99,8 @@ EXPORTS = ("dot_default_options", "dot_workspace_bytes", "dot_create", "dot_solv
            "dot_launch_count", "dot_profile", "dot_profile_read", "dot_kernel_name", "dot_poisson_f32_noalloc",
            "dot_noalloc_last_error", "dot_server_default_options", "dot_server_create", "dot_server_submit",
            "dot_server_wait", "dot_server_result", "dot_server_release", "dot_server_stats",
-           "dot_server_destroy", "dot_server_last_error")
+           "dot_server_destroy", "dot_server_last_error", "dot_solve_multilevel", "dot_prolong_state",
+           "dot_multilevel_last_error")
 
 _lib = None
 _lock = threading.Lock()
@@ -175,5 +176,12 @@ def load(build_if_missing: bool = True):
         lib.dot_server_destroy.restype = None
         lib.dot_server_last_error.argtypes = [vp]
         lib.dot_server_last_error.restype = ctypes.c_char_p
+        lib.dot_solve_multilevel.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                             P(ctypes.c_long)]
+        lib.dot_solve_multilevel.restype = ctypes.c_int
+        lib.dot_prolong_state.argtypes = [P(DotGrid), P(DotGrid), dp, dp, dp, dp, dp, dp]
+        lib.dot_prolong_state.restype = ctypes.c_int
+        lib.dot_multilevel_last_error.argtypes = []
+        lib.dot_multilevel_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib

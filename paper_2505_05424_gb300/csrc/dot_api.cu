@@ -172,6 +172,22 @@ struct dot_ctx {
   long prof_cnt[KID_COUNT] = {0};
 };
 
+void dot::problem_of(const dot_ctx* c, dot_grid* g, dot_options* opt, void** stream, std::vector<double>* rho0,
+                     std::vector<double>* rho1, std::vector<uint8_t>* mask, bool* has_mask) {
+  *g = c->grid;
+  *opt = c->opt;
+  *stream = (void*)c->stream;
+  *rho0 = c->m0;
+  *rho1 = c->m1;
+  mask->assign(c->omega.size(), 0);
+  *has_mask = false;
+  for (size_t i = 0; i < c->omega.size(); ++i)
+    if (c->omega[i] != 1.0) {
+      (*mask)[i] = 1;
+      *has_mask = true;
+    }
+}
+
 namespace {
 
 const char* const kKernelNames[KID_COUNT] = {

@@ -95,20 +95,21 @@ size_t poisson_scratch_elems(const Geo& g);
 size_t tsolve_smem_bytes(const Geo& g);
 
 // src -> dst (src is preserved), FP32 in and out, for G solves of grid g stored
-// one after the other (G > 1 needs poisson_tc_flow).
-void launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
-                       LaunchCounter lc);
+// one after the other (G > 1 needs poisson_tc_flow).  accum (nullable, two-float,
+// slot-strided like phi): when the tensor-core flow runs, its last pass adds the
+// result into accum instead of writing dst and the call returns true.
+bool launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
+                       LaunchCounter lc, float2* accum);
 // Refined solve of f.b (+ f.blo) into out (two-float, slot-strided like phi) for
 // the G slots of a batch; f.b is overwritten.  have_bsum: f.bsum already holds
-// the partial sums of b (k_assemble_b writes them).
+// the partial sums of b.
 constexpr int kBsumParts = 608;   // most partial sums per slot
 void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
                                bool have_bsum, cudaStream_t s, LaunchCounter lc);
-// Line 2 of an iteration, warm-started from the current phi (two-float): one FP32
-// solve of the exact residual b - mean(b) - A^*A phi, added to phi.  Needs the
-// partial sums of b from k_assemble_b; uses f.r and f.phi1 as scratch.
-void launch_poisson_increment_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
-                                 LaunchCounter lc);
+// Lines 1-2 of an iteration: b-assembly fused with the warm-start residual
+// (b never stored), one solve, phi += delta.
+void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                              LaunchCounter lc);
 // Lines 1-6 of Algorithm 2 for every active slot (unfused kernels; penalties from f.sp).
 void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
                        LaunchCounter lc);
@@ -117,7 +118,6 @@ void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& 
 // nsocp per slot; when given, they replace the z-based term.
 void launch_kkt_mx(const Geo& g, int G, const MxFields& f, double* partials, double* out,
                    const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc);
-void launch_assemble_b_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc);
 
 // Fused lines 3-6 for D = 2 (k_fused2d.cu) for every active slot: reads q, alpha,
 // beta of f, writes those of fn; phi, somega, sp from f.  socp_part:

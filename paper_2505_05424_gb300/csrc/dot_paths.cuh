@@ -19,6 +19,10 @@ int check_options(const dot_options& o, std::string* why);
 int prepare_densities(const Geo& g, const double* rho0, const double* rho1, const uint8_t* mask,
                       double obstacle_weight, std::vector<double>* m0, std::vector<double>* m1,
                       std::vector<double>* omega, bool* any_mask, std::string* why);
+// The problem a context solves: grid, options, stream, densities (c, any scale)
+// and the obstacle mask (cells whose weight is not 1).
+void problem_of(const dot_ctx* c, dot_grid* g, dot_options* opt, void** stream, std::vector<double>* rho0,
+                std::vector<double>* rho1, std::vector<uint8_t>* mask, bool* has_mask);
 // Stopping measures of Sec. 5.3 (kkt[DOT_KKT_LEN]) from the reduction slots r;
 // cn2 = sum of squares of c.
 void kkt_measures(const Geo& g, double cn2, const double* r, long iters, double sigma, double* kkt);

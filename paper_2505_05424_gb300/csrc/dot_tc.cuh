@@ -7,8 +7,9 @@
 
 namespace dot {
 
-// The tcgen05 pass handles axis lengths 1 <= K <= 256 (one TMEM accumulator
-// tile); rows of X and of the tables are stored with strides that are multiples
+// The tcgen05 pass handles axis lengths 1 <= K <= 4096: each CTA computes up to
+// 256 output columns in one TMEM accumulator, longer axes use several column
+// tiles.  Rows of X and of the tables are stored with strides that are multiples
 // of 4 floats (16-byte TMA row strides).
 bool tc_pass_supported(int K);
 int tc_smem_bytes();
@@ -32,6 +33,8 @@ struct TcPass {
   int M, ldo;           // ROWS_FLAT: runs of M rows written with stride ldo; KEEP: output row stride
   const Geo* geo;       // KEEP: grid of one group (rows r map to in-plane index r mod P)
   const float* lam[4];  // KEEP: eigenvalues, lam[0] along the transformed axis
+  float2* accum;        // ROWS_A (nullable): add the result into this two-float field (same
+                        // layout as out) instead of writing out
   int* err;             // set by a CTA whose pipeline wait timed out
 };
 // Returns false when the pass cannot run on the tensor cores (unsupported K,

@@ -39,6 +39,7 @@
 
 #include "dot_internal.cuh"
 #include "dot_tc.cuh"
+#include "ffloat.cuh"
 
 namespace dot {
 namespace {
@@ -150,7 +151,8 @@ __device__ __forceinline__ float tf32_rna(float x) {
 struct PassArgs {
   float* out;
   int K;           // length of the transformed axis (= reduction length)
-  int Nout;        // output frequencies computed (MMA N, multiple of 16, <= 256)
+  int Nout;        // output columns per CTA (MMA N, multiple of 16, <= 256); CTA column
+                   // tile blockIdx.y covers frequencies [256 * blockIdx.y, + Nout)
   int mode;        // TC_ROWS_FLAT, TC_ROWS_A, TC_KEEP
   long long R;     // ROWS_FLAT / KEEP: total rows (all groups)
   int A, Bd, G;    // ROWS_FLAT: rows per group A; ROWS_A: extents of a, b; G groups
@@ -163,6 +165,7 @@ struct PassArgs {
   int N[kMaxD];
   unsigned P;
   FastDiv fP, fS[kMaxD], fN[kMaxD];
+  float2* accum;   // ROWS_A: accumulate into a two-float field instead of writing out
   int* err;
 };
 
@@ -225,6 +228,9 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
+  // this CTA's output columns: [n0, n0 + nout)
+  const int n0 = blockIdx.y * kMaxN;
+  const int nout = min(pa.Nout, (pa.K - n0 + 15) / 16 * 16);
   if (warp == 0) {
     if (lane == 0) {
       const unsigned bytes = kXBytes + 2u * (unsigned)pa.Nout * kChunkK * 4u;
@@ -235,13 +241,13 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
         mbar_expect_tx(&full[s], bytes);
         if (pa.mode != TC_ROWS_A) tma_load_2d(sx[s], &tm_x, &full[s], c * kChunkK, (int)row0);
         else tma_load_4d(sx[s], &tm_x, &full[s], c * kChunkK, bfix, a0, gfix);
-        tma_load_2d(sbh[s], &tm_bhi, &full[s], c * kChunkK, 0);
-        tma_load_2d(sbl[s], &tm_blo, &full[s], c * kChunkK, 0);
+        tma_load_2d(sbh[s], &tm_bhi, &full[s], c * kChunkK, n0);
+        tma_load_2d(sbl[s], &tm_blo, &full[s], c * kChunkK, n0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32(kTileM, pa.Nout);
+      const uint32_t idesc = idesc_tf32(kTileM, nout);
       for (int c = 0; c < nchunks; ++c) {
         const int s = c % kStages, it = c / kStages;
         if (!mbar_wait(&conv[s], it & 1)) { atomicExch(&s_fail, 1); break; }
@@ -325,7 +331,7 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
           }
         }
       }
-      for (int c0 = 0; c0 < pa.Nout; c0 += 16) {
+      for (int c0 = 0; c0 < nout; c0 += 16) {
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0;
         asm volatile(
@@ -339,23 +345,33 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
           float w[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int k = c0 + j;
+            const int k = n0 + c0 + j;
             const float lam = (k < pa.K ? pa.lam[0][k] : 1.f) + lsp;
             w[j] = (k == 0 && zero_mode) ? 0.f : __uint_as_float(v[j]) / lam;
           }
-          float* o = pa.out + out_base + c0;
-          if (c0 + 16 <= pa.K) {
+          float* o = pa.out + out_base + n0 + c0;
+          if (n0 + c0 + 16 <= pa.K) {
 #pragma unroll
             for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
           } else {
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              if (c0 + j < pa.K) o[j] = w[j];
+              if (n0 + c0 + j < pa.K) o[j] = w[j];
           }
+        } else if (pa.accum) {
+          // all 16 loads first, then the stores: no load waits behind a store
+          float2 old[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (n0 + c0 + j < pa.K) old[j] = pa.accum[out_base + (long long)(n0 + c0 + j) * col_stride];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (n0 + c0 + j < pa.K)
+              pa.accum[out_base + (long long)(n0 + c0 + j) * col_stride] = ff_add_f(old[j], __uint_as_float(v[j]));
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int k = c0 + j;
+            const int k = n0 + c0 + j;
             if (k < pa.K) pa.out[out_base + (long long)k * col_stride] = __uint_as_float(v[j]);
           }
         }
@@ -407,7 +423,7 @@ bool encode_tensor_map(CUtensorMap* m, CUtensorMapDataType type, int rank, const
   return r == CUDA_SUCCESS;
 }
 
-bool tc_pass_supported(int K) { return K >= 1 && K <= kMaxN; }
+bool tc_pass_supported(int K) { return K >= 1 && K <= 16 * kMaxN; }
 
 int tc_smem_bytes() { return kSmemBytes; }
 
@@ -420,7 +436,7 @@ bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
   const int K = p.K;
   if (!tc_pass_supported(K) || p.ldx < K || p.ldx % 4 != 0 || p.ldb < K || p.ldb % 4 != 0) return false;
   if (((uintptr_t)p.X & 15) || ((uintptr_t)p.Bhi & 15) || ((uintptr_t)p.Blo & 15)) return false;
-  const int Nout = (K + 15) / 16 * 16;
+  const int Nout = K < kMaxN ? (K + 15) / 16 * 16 : kMaxN;
   CUtensorMap mx, mh, ml;
   bool ok;
   if (p.mode != TC_ROWS_A) {
@@ -455,6 +471,8 @@ bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
   pa.fA = make_fastdiv((unsigned)pa.A);
   pa.fM = make_fastdiv((unsigned)pa.M);
   pa.err = p.err;
+  pa.accum = p.mode == TC_ROWS_A ? p.accum : nullptr;
+  if (p.accum && p.mode != TC_ROWS_A) return false;
   if (p.mode == TC_ROWS_FLAT && (p.R % pa.A != 0 || pa.A % pa.M != 0 || pa.ldo < pa.M)) return false;
   if (p.mode == TC_KEEP) {
     if (!p.geo || pa.ldo < K || pa.ldo % 4 != 0 || ((uintptr_t)p.out & 15)) return false;
@@ -469,8 +487,9 @@ bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
     pa.P = (unsigned)g.P;
     pa.fP = g.fP;
   }
-  unsigned grid = p.mode != TC_ROWS_A ? (unsigned)((p.R + kTileM - 1) / kTileM)
-                                      : (unsigned)(pa.G * pa.Bd * ((p.A + kTileM - 1) / kTileM));
+  dim3 grid(p.mode != TC_ROWS_A ? (unsigned)((p.R + kTileM - 1) / kTileM)
+                                 : (unsigned)(pa.G * pa.Bd * ((p.A + kTileM - 1) / kTileM)),
+            (unsigned)((K + kMaxN - 1) / kMaxN));
   k_dct_pass_tc<<<grid, kThreadsTC, smem_bytes(Nout), s>>>(mx, mh, ml, pa);
   return true;
 }

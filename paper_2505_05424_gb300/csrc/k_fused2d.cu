@@ -539,12 +539,6 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
     const int bcur = t % 3, bprev = (t + 2) % 3;
     const float2* tcur = btiles + bcur * kBetaTile;
     const float2* tprev = btiles + bprev * kBetaTile;
-    // prefetch the next cone time's beta into the buffer freed at the end of step t-1
-    if (tid == 0 && t + 1 <= tlast_cone) {
-      const int nb = (t + 1) % 3;
-      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1, slot);
-      inflight[nb] = true;
-    }
     if (t <= g.T - 1) {
       const bool ok = bar_wait(&bars[bcur], phase[bcur]);
       if (ok) {
@@ -552,6 +546,13 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
         inflight[bcur] = false;
       }
       if (__syncthreads_or(!ok)) { failed = true; break; }
+    }
+    // prefetch the next cone time's beta into buffer (t+1) % 3 = (t-2) % 3, whose
+    // last reader (step C of t-1) every thread has left at the barrier above
+    if (tid == 0 && t + 1 <= tlast_cone) {
+      const int nb = (t + 1) % 3;
+      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1, slot);
+      inflight[nb] = true;
     }
     // ---------------- A: cones at time t ----------------
     if (t <= g.T - 1) {
@@ -701,7 +702,9 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
     q0p = q0c;
 #pragma unroll
     for (int j = 0; j < K2; ++j) zp[j] = zc[j];
-    __syncthreads();
+    // no barrier here: step A of t+1 writes only zt[lev of t+1] (read by step B of
+    // t, which every thread finished before step C) and registers; step B of t+1,
+    // which overwrites the faces step C reads, follows the barrier after A
   }
   if (failed) {
     // a tile load did not complete in time: wait (bounded) for the loads this

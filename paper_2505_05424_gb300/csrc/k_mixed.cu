@@ -36,9 +36,7 @@ __device__ __forceinline__ float2 grad_pair(const float2* phi, long long i, long
 // A phi - q with one rounding relative to the (small) difference itself.
 __device__ __forceinline__ float grad_minus(float2 g, float q) { return (g.x - q) + g.y; }
 
-// Line 1: b = A^*(q - alpha/sigma) - c/sigma in two-float arithmetic (alpha/sigma
-// and c/sigma are 10-10^3 times the O(1) part that survives their cancellation).
-constexpr int kMeanBlocks = kBsumParts;   // blocks of the zero-mode partial sums
+constexpr int kMeanBlocks = kBsumParts;   // offset of mean(b) in a slot's bsum
 
 // FP64 sum of a block's per-thread two-float partials into out[blockIdx.x].
 __device__ __forceinline__ void block_sum_ff(float2 v, double* out) {
@@ -54,66 +52,19 @@ __device__ __forceinline__ void block_sum_ff(float2 v, double* out) {
   }
 }
 
-// Zero-mode partial sums per slot: one per block of the b-assembly.
+// Zero-mode partial sums per slot: one per block of k_sum_b.
 inline int bsum_blocks(const Geo& g) {
   const long long nn = (long long)(g.T + 1) * g.P;
   long long b = (nn + kThreads - 1) / kThreads;
   return (int)(b < kBsumParts ? (b < 1 ? 1 : b) : kBsumParts);
 }
 
-template <int D>
-__global__ void k_assemble_b(Geo g, MxFields fb) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const float2 isg = fb.sp[slot].isg;
-  const MxFields f = slot_view(fb, g, slot);
-  const long long n = (long long)(g.T + 1) * g.P;
-  float2 bsum = make_float2(0.f, 0.f);   // this thread's part of sum(b): the zero mode
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int t = plane_of(g, i);
-    const long long p = i - (long long)t * g.P;
-    const float ih0 = (float)g.invh[0];
-    float2 acc = make_float2(0.f, 0.f);
-    if (t >= 1) {
-      const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i - g.P], isg)), f.q[0][i - g.P]);
-      acc = ff_add(acc, ff_mul_f(w, ih0));
-    }
-    if (t < g.T) {
-      const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i], isg)), f.q[0][i]);
-      acc = ff_add(acc, ff_neg(ff_mul_f(w, ih0)));
-    }
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int x = coord(g, p, d);
-      const float* qd = f.q[1 + d];
-      const float2* ad = f.al[1 + d];
-      const long long s = g.sst[d];
-      const float ih = (float)g.invh[1 + d];
-      if (x >= 1) {
-        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i - s], isg)), qd[i - s]);
-        acc = ff_add(acc, ff_mul_f(w, ih));
-      }
-      if (x <= g.N[d] - 2) {
-        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i], isg)), qd[i]);
-        acc = ff_add(acc, ff_neg(ff_mul_f(w, ih)));
-      }
-    }
-    if (t == 0) acc = ff_add(acc, ff_neg(ff_mul(f.c0[p], isg)));
-    if (t == g.T) acc = ff_add(acc, ff_mul(f.c1[p], isg));
-    f.b[i] = acc.x;
-    f.blo[i] = acc.y;
-    bsum = ff_add(bsum, acc);
-  }
-  block_sum_ff(bsum, f.bsum);
-}
-
 // Sum of b (per-block partials, two-float per thread, FP64 per block): the exact
 // zero mode of the right-hand side.  An FP32 DCT of a field with a large mean
 // leaks O(u_32 * mean * sqrt(n)) into the other coefficients; removing the exact
 // mean from the refinement residual lets the correction solve remove that leak.
-// The iteration gets these partials from k_assemble_b; the Poisson operator entry
-// points use this kernel.
+// The refined Poisson operator (dot_poisson and the allocation-free entry point)
+// uses it.
 __global__ void k_sum_b(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
@@ -191,49 +142,76 @@ __global__ void k_residual(Geo g, MxFields fb) {
 }
 
 // Line 2 warm-started from the previous iteration's potential:
-//   r = b - mean(b) - A^*A phi^k,  delta = P(r),  phi^{k+1} = phi^k + delta.
+//   r = b - A^*A phi^k,  delta = P(r),  phi^{k+1} = phi^k + delta.
 // A^*A phi^k is accumulated from exact two-float neighbour differences of the
 // two-float phi^k, so r is exact up to its final rounding to FP32 and the new
 // potential carries the FP32 solve's relative error times |phi^{k+1} - phi^k|
 // only (the inexact subproblem solves Algorithm 1 admits; phi^0 = 0 makes the
-// first step a plain solve).
+// first step a plain solve).  a - b of two two-float values, unnormalised:
 __device__ __forceinline__ float2 ff_diff(float2 a, float2 b) {
   const float2 d = two_sum(a.x, -b.x);
   return make_float2(d.x, d.y + (a.y - b.y));
 }
 
+// Lines 1 and 2 fused: b = A^*(q - alpha/sigma) - c/sigma at a node, in
+// two-float arithmetic (alpha/sigma and c/sigma are 10-10^3 times the O(1) part
+// that survives their cancellation), and at once the warm-start residual
+// r = b - A^*A phi^k, so b never reaches memory.  mean(b) is not subtracted: the
+// equal masses make sum(b) vanish up to rounding (|sum b| ~ 1e-16 |c| / sigma),
+// and the solve drops the zero mode.
 template <int D>
-__global__ void k_residual_phi(Geo g, MxFields fb) {
+__global__ void k_assemble_residual(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
+  const float2 isg = fb.sp[slot].isg;
   const MxFields f = slot_view(fb, g, slot);
-  const float2 mean = reinterpret_cast<const float2*>(f.bsum + kMeanBlocks)[0];
   const long long n = (long long)(g.T + 1) * g.P;
   const float2* x = f.phi;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
+    const float ih0 = (float)g.invh[0];
+    float2 acc = make_float2(0.f, 0.f);    // b
+    float2 lap = make_float2(0.f, 0.f);    // A^*A phi
     const float2 xi = x[i];
-    float2 acc = make_float2(0.f, 0.f);
     {
-      float2 s = make_float2(0.f, 0.f);
-      if (t >= 1) s = ff_add(s, ff_diff(xi, x[i - g.P]));
-      if (t < g.T) s = ff_add(s, ff_diff(xi, x[i + g.P]));
-      const float ih = (float)g.invh[0];
-      acc = ff_add(acc, ff_mul_f(s, ih * ih));
+      float2 sd = make_float2(0.f, 0.f);
+      if (t >= 1) {
+        const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i - g.P], isg)), f.q[0][i - g.P]);
+        acc = ff_add(acc, ff_mul_f(w, ih0));
+        sd = ff_add(sd, ff_diff(xi, x[i - g.P]));
+      }
+      if (t < g.T) {
+        const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i], isg)), f.q[0][i]);
+        acc = ff_add(acc, ff_neg(ff_mul_f(w, ih0)));
+        sd = ff_add(sd, ff_diff(xi, x[i + g.P]));
+      }
+      lap = ff_add(lap, ff_mul_f(sd, ih0 * ih0));
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const int xd = coord(g, p, d);
-      const long long st = g.sst[d];
-      float2 s = make_float2(0.f, 0.f);
-      if (xd >= 1) s = ff_add(s, ff_diff(xi, x[i - st]));
-      if (xd <= g.N[d] - 2) s = ff_add(s, ff_diff(xi, x[i + st]));
+      const float* qd = f.q[1 + d];
+      const float2* ad = f.al[1 + d];
+      const long long s = g.sst[d];
       const float ih = (float)g.invh[1 + d];
-      acc = ff_add(acc, ff_mul_f(s, ih * ih));
+      float2 sd = make_float2(0.f, 0.f);
+      if (xd >= 1) {
+        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i - s], isg)), qd[i - s]);
+        acc = ff_add(acc, ff_mul_f(w, ih));
+        sd = ff_add(sd, ff_diff(xi, x[i - s]));
+      }
+      if (xd <= g.N[d] - 2) {
+        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i], isg)), qd[i]);
+        acc = ff_add(acc, ff_neg(ff_mul_f(w, ih)));
+        sd = ff_add(sd, ff_diff(xi, x[i + s]));
+      }
+      lap = ff_add(lap, ff_mul_f(sd, ih * ih));
     }
-    const float2 r = ff_add(make_float2(f.b[i], f.blo[i]), ff_neg(ff_add(acc, mean)));
+    if (t == 0) acc = ff_add(acc, ff_neg(ff_mul(f.c0[p], isg)));
+    if (t == g.T) acc = ff_add(acc, ff_mul(f.c1[p], isg));
+    const float2 r = ff_add(acc, ff_neg(lap));
     f.r[i] = r.x + r.y;
   }
 }
@@ -645,35 +623,39 @@ void poisson_refined_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisso
     lc.launched(KID_RESIDUAL);
   }
   k_mean_b<<<G, kThreads, 0, s>>>(g, f, nb);
-  launch_poisson_mx(g, G, ps, f.b, f.phi1, s, lc);
+  launch_poisson_mx(g, G, ps, f.b, f.phi1, s, lc, nullptr);
   k_residual<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
   lc.launched(KID_RESIDUAL, 2);
-  launch_poisson_mx(g, G, ps, f.r, f.b, s, lc);
+  launch_poisson_mx(g, G, ps, f.r, f.b, s, lc, nullptr);
   k_combine<<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f, out);
   lc.launched(KID_COMBINE);
 }
 
-// Line 2 for an iteration: the warm-started solve above (the partial sums of b
-// come from k_assemble_b).
-template <int D>
-void poisson_increment_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
-                            LaunchCounter lc) {
+// delta = P(f.r), phi += delta: the last DCT pass adds into phi when it runs on
+// the tensor cores; otherwise delta goes through phi1 and one more kernel.
+void poisson_add_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                      LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P;
-  k_mean_b<<<G, kThreads, 0, s>>>(g, f, bsum_blocks(g));
-  k_residual_phi<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
-  lc.launched(KID_RESIDUAL, 2);
-  launch_poisson_mx(g, G, ps, f.r, f.phi1, s, lc);
+  if (launch_poisson_mx(g, G, ps, f.r, f.phi1, s, lc, f.phi)) return;
   k_phi_add<<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
   lc.launched(KID_COMBINE);
+}
+
+// Lines 1 and 2 of an iteration (fused b-assembly and residual, one solve).
+template <int D>
+void assemble_solve_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                         LaunchCounter lc) {
+  const long long nn = (long long)(g.T + 1) * g.P;
+  k_assemble_residual<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f);
+  lc.launched(KID_ASSEMBLE_B);
+  poisson_add_tmpl(g, G, f, ps, s, lc);
 }
 
 template <int D>
 void launch_iter_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
                       LaunchCounter lc) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
-  k_assemble_b<D><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);              // line 1
-  lc.launched(KID_ASSEMBLE_B);
-  poisson_increment_tmpl<D>(g, G, f, ps, s, lc);                                   // line 2
+  assemble_solve_tmpl<D>(g, G, f, ps, s, lc);                                      // lines 1-2
   k_project<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                   // line 3
   lc.launched(KID_PROJECT);
   k_update_q0<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                 // lines 4-5
@@ -711,22 +693,16 @@ void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxP
   else poisson_refined_tmpl<3>(g, G, f, ps, out, have_bsum, s, lc);
 }
 
-void launch_poisson_increment_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
-                                 LaunchCounter lc) {
-  if (g.D == 2) poisson_increment_tmpl<2>(g, G, f, ps, s, lc);
-  else poisson_increment_tmpl<3>(g, G, f, ps, s, lc);
+void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                              LaunchCounter lc) {
+  if (g.D == 2) assemble_solve_tmpl<2>(g, G, f, ps, s, lc);
+  else assemble_solve_tmpl<3>(g, G, f, ps, s, lc);
 }
 
 void launch_kkt_mx(const Geo& g, int G, const MxFields& f, double* partials, double* out,
                    const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc) {
   if (g.D == 2) launch_kkt_tmpl<2>(g, G, f, partials, out, socp_part, nsocp, s, lc);
   else launch_kkt_tmpl<3>(g, G, f, partials, out, socp_part, nsocp, s, lc);
-}
-
-void launch_assemble_b_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc) {
-  if (g.D == 2) k_assemble_b<2><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);
-  else k_assemble_b<3><<<dim3(bsum_blocks(g), G), kThreads, 0, s>>>(g, f);
-  lc.launched(KID_ASSEMBLE_B);
 }
 
 long long kkt_partials_len_mx(const Geo& g) { return kkt_partials_len_slot(g); }

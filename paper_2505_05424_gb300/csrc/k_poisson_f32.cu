@@ -266,12 +266,12 @@ void launch_tsolve(const Geo& g, const MxPoisson& ps, const float* X, float* Y, 
   }
 }
 
-// The tensor-core flow applies when every axis fits one tcgen05 tile and the
-// spatial rows have 16-byte strides.
+// The tensor-core flow applies when every axis is within the tcgen05 pass's
+// range and the spatial rows have 16-byte strides.
 bool poisson_tc_flow(const Geo& g, const MxPoisson& ps) {
-  if (!ps.use_tc || !ps.tpad[0] || g.T + 1 > 256) return false;
+  if (!ps.use_tc || !ps.tpad[0] || !tc_pass_supported(g.T + 1)) return false;
   for (int d = 0; d < g.D; ++d)
-    if (g.N[d] > 256 || g.N[d] % 4 != 0) return false;
+    if (!tc_pass_supported(g.N[d]) || g.N[d] % 4 != 0) return false;
   return true;
 }
 
@@ -295,7 +295,7 @@ bool tc_pass(const MxPoisson& ps, TcPass p, int axis, bool inverse, cudaStream_t
 
 // The tensor-core flow for G solves stored one after the other.
 bool poisson_tc(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
-                LaunchCounter lc) {
+                LaunchCounter lc, float2* accum) {
   const long long nn = (long long)(g.T + 1) * g.P;
   const int M = g.T + 1, ldt = time_ld(g);
   float* w[2] = {ps.w1, ps.w2};
@@ -376,6 +376,7 @@ bool poisson_tc(const Geo& g, int G, const MxPoisson& ps, const float* src, floa
       p.A = (int)(g.P / K);
       p.Bd = M;
       p.G = G;
+      p.accum = accum;
     }
     if (!tc_pass(ps, p, a, true, s, lc)) return false;
     cur = p.out;
@@ -386,9 +387,9 @@ bool poisson_tc(const Geo& g, int G, const MxPoisson& ps, const float* src, floa
 
 }  // namespace
 
-void launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
-                       LaunchCounter lc) {
-  if (poisson_tc_flow(g, ps) && poisson_tc(g, G, ps, src, dst, s, lc)) return;
+bool launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* src, float* dst, cudaStream_t s,
+                       LaunchCounter lc, float2* accum) {
+  if (poisson_tc_flow(g, ps) && poisson_tc(g, G, ps, src, dst, s, lc, accum)) return accum != nullptr;
   // SIMT flow (one solve)
   const long long n = (long long)(g.T + 1) * g.P;
   float* w[2] = {ps.w1, ps.w2};
@@ -416,6 +417,7 @@ void launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* sr
     spatial_pass(ps, a, true, cur(), out, K, n, mode, A, Bd, s, lc);
     if (!last) ci = next();
   }
+  return false;
 }
 
 }  // namespace dot

@@ -329,8 +329,7 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
   if (fused_) {
     const MxFields& fc = cur();
     const MxFields& fn = other();
-    launch_assemble_b_mx(g_, G_, fc, s, lc);                                // line 1
-    launch_poisson_increment_mx(g_, G_, fc, ps_, s, lc);                     // line 2 (warm-started)
+    launch_assemble_solve_mx(g_, G_, fc, ps_, s, lc);                       // lines 1-2 (warm-started)
     if (!(tma_ && launch_fused2d_tma(g_, G_, fc, fn, B_->socp, B_->err, s, lc)))
       launch_fused2d(g_, G_, fc, fn, B_->socp, s, lc);                       // lines 3-6
     cur_ ^= 1;

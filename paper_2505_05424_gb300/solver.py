@@ -172,6 +172,15 @@ class DotSolver:
         self._check(self.lib.dot_poisson(self.ctx, _dp(b), _dp(phi)))
         return phi
 
+    def dot_solve_multilevel(self, levels: int, tol: float = 1e-6, maxit: int = 100000, coarse_tol: float = 0.0):
+        """(status, iterations per level, finest first) of dot_solve_multilevel;
+        coarse_tol <= 0 selects the paper's per-level tolerance."""
+        it = (ctypes.c_long * (int(levels) + 1))()
+        rc = self.lib.dot_solve_multilevel(self.ctx, int(levels), float(tol), float(coarse_tol), int(maxit), it)
+        if rc not in (N.DOT_OK, N.DOT_ENOTCONV):
+            raise DotError(rc, self.lib.dot_multilevel_last_error().decode())
+        return rc, [int(v) for v in it]
+
     def dot_profile(self, enable: bool = True):
         self._check(self.lib.dot_profile(self.ctx, int(bool(enable))))
 
@@ -332,3 +341,21 @@ class DotServer:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dot_prolong_state(D: int, Tc: int, Nc, Tf: int, Nf, q, alpha, beta):
+    """Binding of dot_prolong_state (host only): the coarse state (q, alpha, beta in
+    the layouts of dot_get_state) interpolated onto the fine grid."""
+    lib = N.load()
+    gc, gf = make_grid(D, Tc, Nc), make_grid(D, Tf, Nf)
+    Ns = [int(Nf)] * D if np.isscalar(Nf) else [int(n) for n in Nf]
+    Pf = int(np.prod(Ns))
+    nq = Tf * Pf + sum((Tf + 1) * (Pf // Ns[d]) * (Ns[d] - 1) for d in range(D))
+    nb = (4 * D + 2) * Tf * Pf
+    qf, af, bf = np.zeros(nq), np.zeros(nq), np.zeros(nb)
+    q, alpha, beta = _f64(q).ravel(), _f64(alpha).ravel(), _f64(beta).ravel()
+    rc = lib.dot_prolong_state(ctypes.byref(gc), ctypes.byref(gf), _dp(q), _dp(alpha), _dp(beta), _dp(qf),
+                               _dp(af), _dp(bf))
+    if rc != N.DOT_OK:
+        raise DotError(rc, lib.dot_multilevel_last_error().decode())
+    return qf, af, bf

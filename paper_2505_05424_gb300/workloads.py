@@ -39,6 +39,7 @@ GAUSS32 = GridSpec(2, 16, 32)        # 2D 32^2 x 16, two Gaussians + floor 1e-3
 MIX256 = GridSpec(2, 64, 256)        # 2D 256^2 x 64, Gaussian mixtures with exact zeros
 OBST128 = GridSpec(2, 32, 128)       # 2D 128^2 x 32, mixtures + rectangle obstacles
 MIX3D64 = GridSpec(3, 32, 64)        # 3D 64^3 x 32, anisotropic mixtures + floor 1e-4
+MIX1024 = GridSpec(2, 32, 1024)      # 2D 1024^2 x 32, mixtures as MIX256 (the scalability case)
 
 
 def cell_centres(N: int, D: int):
@@ -142,6 +143,9 @@ def workload(name: str, seed: int | None = None):
     if name == "obst128":
         r0, r1, m = mixture_pair(OBST128, 1003 if seed is None else seed, obstacles=True)
         return OBST128, r0, r1, m
+    if name == "mix1024":
+        r0, r1, m = mixture_pair(MIX1024, 1005 if seed is None else seed)
+        return MIX1024, r0, r1, m
     if name == "mix3d64":
         r0, r1, m = mixture_pair(MIX3D64, 1004 if seed is None else seed)
         return MIX3D64, r0, r1, m

@@ -26,10 +26,11 @@ def _lib():
 
 
 # odd sizes (SIMT DCT passes), and axis lengths divisible by 4 (tensor-core DCT
-# passes) with row counts that leave ragged 128-row tiles, up to a 256-long axis
+# passes) with row counts that leave ragged 128-row tiles, up to a 300-long axis
+# (two 256-column output tiles, the second ragged)
 GRIDS = [(2, 4, [6, 5]), (2, 1, [2, 2]), (2, 69, [70, 3]), (2, 7, [9, 131]), (3, 3, [4, 3, 5]),
          (3, 5, [6, 7, 66]), (2, 5, [32, 36]), (2, 9, [256, 64]), (2, 16, [32, 32]), (3, 3, [8, 12, 16]),
-         (2, 64, [128, 128])]
+         (2, 64, [128, 128]), (2, 3, [8, 300])]
 
 
 def f32(a):
@@ -58,7 +59,7 @@ def test_refined_poisson(D, T, N):
     gpu.close()
 
 
-@pytest.mark.parametrize("D,T,N", [(2, 5, [32, 36]), (2, 64, [128, 128]), (3, 3, [8, 12, 16])])
+@pytest.mark.parametrize("D,T,N", [(2, 5, [32, 36]), (2, 64, [128, 128]), (3, 3, [8, 12, 16]), (2, 3, [8, 300])])
 def test_poisson_runs_entirely_on_tensor_cores(D, T, N):
     """Every axis fits a tcgen05 tile: each of the two solves of a refined Poisson
     solve is D spatial passes each way plus two time passes, none on the SIMT
