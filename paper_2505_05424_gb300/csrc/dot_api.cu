@@ -448,7 +448,7 @@ int dot_set_state(dot_ctx* c, const double* q, const double* alpha, const double
   if (!q || !alpha || !beta) return fail(c, DOT_EINVAL, "q, alpha and beta are required");
   if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(c, DOT_EINVAL, "sigma must be > 0");
   std::string perr;
-  int rc = c->path->write_state(q, alpha, beta, c->stream, &perr);
+  int rc = c->path->write_state(q, alpha, beta, sigma, c->stream, &perr);
   if (rc != DOT_OK) return fail(c, rc, perr);
   c->sigma = sigma;
   c->iters = iters;

@@ -34,7 +34,15 @@ class MixedBatch {
   int load_slot(int b, const std::vector<double>& m0, const std::vector<double>& m1,
                 const std::vector<double>* omega, double sigma, double tau, cudaStream_t s, std::string* err);
   // Host copy of the slot parameters; upload_params copies them to the device.
-  void set_sigma(int b, double sigma, double tau);
+  // set_sigma with rescale: the slot's stored multipliers (alpha/sigma, beta/sigma)
+  // belong to the old sigma and are rescaled by the next apply_rescale.
+  void set_sigma(int b, double sigma, double tau, bool rescale);
+  double sigma(int b) const { return hs_[b]; }
+  // Rescale the stored multipliers of every slot whose sigma changed (one kernel;
+  // it reads the factors from the device parameters), and mark them done on the host.
+  void apply_rescale(cudaStream_t s, LaunchCounter lc);
+  void clear_rescale();
+  bool rescale_pending() const;
   void set_active(int b, bool on);
   bool active(int b) const { return hp_[b].active != 0; }
   cudaError_t upload_params(cudaStream_t s);
@@ -55,8 +63,8 @@ class MixedBatch {
 
   int read_fields(int b, double* rho, double* m, double* phi, cudaStream_t s, std::string* err);
   int read_state(int b, double* q, double* al, double* beta, cudaStream_t s, std::string* err);
-  int write_state(int b, const double* q, const double* al, const double* beta, cudaStream_t s,
-                  std::string* err);
+  int write_state(int b, const double* q, const double* al, const double* beta, double sigma, double tau,
+                  cudaStream_t s, std::string* err);
   // The refined Poisson operator on slot 0's scratch.
   int poisson_op(const double* b, double* phi, cudaStream_t s, LaunchCounter lc, std::string* err);
 
@@ -74,6 +82,7 @@ class MixedBatch {
   int* err_ = nullptr;
   SlotParam* dparams_ = nullptr;
   std::vector<SlotParam> hp_;
+  std::vector<double> hs_;   // sigma per slot (host)
   std::vector<std::vector<float>> hT_;
 
   const MxFields& cur() const;

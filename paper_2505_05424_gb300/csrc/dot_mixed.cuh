@@ -7,9 +7,12 @@ namespace dot {
 // Per-solve scalars of a batch, read by the kernels from device memory so that a
 // captured launch sequence serves every penalty value.
 struct SlotParam {
-  float2 isg;   // 1/sigma as a two-float
-  float ts;     // tau * sigma
-  int active;   // 0: the slot holds no solve; its blocks return at once
+  float2 isg;      // 1/sigma (two-float): scales c in the b-assembly
+  float2 sg;       // sigma (two-float): turns the stored alpha/sigma, beta/sigma into alpha, beta
+  float2 rescale;  // sigma_old / sigma_new, applied to the stored multipliers before the next
+                   // iteration after a penalty change (1: nothing to do)
+  float tau;       // step length tau of the multiplier updates
+  int active;      // 0: the slot holds no solve; its blocks return at once
 };
 
 // A batch holds G solves of one grid.  Every per-solve field below is stored as
@@ -17,8 +20,8 @@ struct SlotParam {
 // eigenvalues are shared.
 struct MxFields {
   float* q[kMaxD + 1];     // q_0: T*P; q_d: (T+1)*P padded
-  float2* al[kMaxD + 1];   // two-float multipliers, same shapes as q
-  float2* beta;            // K * T * P two-float multipliers
+  float2* al[kMaxD + 1];   // alpha / sigma (two-float), same shapes as q
+  float2* beta;            // beta / sigma (two-float), K * T * P
   float* z;                // K * T * P
   float2* phi;             // (T+1)*P two-float potential
   float* b;                // (T+1)*P right-hand side, high part; reused for the correction delta
@@ -106,6 +109,9 @@ bool launch_poisson_mx(const Geo& g, int G, const MxPoisson& ps, const float* sr
 constexpr int kBsumParts = 608;   // most partial sums per slot
 void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
                                bool have_bsum, cudaStream_t s, LaunchCounter lc);
+// Multiply the stored alpha/sigma and beta/sigma of every slot whose rescale
+// factor is not 1 by that factor (after a penalty change).
+void launch_rescale_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc);
 // Lines 1-2 of an iteration: b-assembly fused with the warm-start residual
 // (b never stored), one solve, phi += delta.
 void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,

@@ -173,7 +173,12 @@ extern "C" int dot_poisson_f32_noalloc(const dot_grid* grid, const float* b, flo
   }
   // the right-hand side is copied in (the solve overwrites it with the correction);
   // its low part and the error flag must start at zero
-  static const SlotParam kOne = {make_float2(0.f, 0.f), 0.f, 1};
+  SlotParam one;
+  std::memset(&one, 0, sizeof(one));
+  one.rescale = make_float2(1.f, 0.f);
+  one.active = 1;
+  static SlotParam kOne;
+  kOne = one;
   e = cudaMemcpyAsync(f.b, b, (size_t)nn * sizeof(float), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(f.blo, 0, (size_t)nn * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ps.err, 0, sizeof(int), s);

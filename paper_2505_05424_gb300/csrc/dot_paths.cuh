@@ -56,7 +56,8 @@ class Path {
   // alpha_0 (natural layout) into rho, alpha_bar (natural layout) into m, phi; NULL = skip.
   virtual int read_fields(double* rho, double* m, double* phi, cudaStream_t s, std::string* err) = 0;
   virtual int read_state(double* q, double* al, double* beta, cudaStream_t s, std::string* err) = 0;
-  virtual int write_state(const double* q, const double* al, const double* beta, cudaStream_t s,
+  // The state with the penalty sigma it belongs to (the next iterate uses sigma).
+  virtual int write_state(const double* q, const double* al, const double* beta, double sigma, cudaStream_t s,
                           std::string* err) = 0;
   virtual int poisson_op(const double* b, double* phi, cudaStream_t s, LaunchCounter lc, std::string* err) = 0;
   // Device flag that a kernel sets when a bounded pipeline wait gave up (or nullptr).

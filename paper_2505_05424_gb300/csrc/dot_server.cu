@@ -256,6 +256,7 @@ void dot_server::launch_period(Batch& b) {
       cudaGraph_t graph = nullptr;
       e = cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
+        b.mb->apply_rescale(b.stream, lc);     // penalty changes since the last period
         for (int it = 0; it < ce; ++it) b.mb->iterate(b.stream, lc);
         b.mb->kkt(b.stream, lc);
         e = cudaStreamEndCapture(b.stream, &graph);
@@ -270,10 +271,12 @@ void dot_server::launch_period(Batch& b) {
     b.mb->set_parity(par ^ (ce & 1));
     launches = b.graph_launches[par];
   } else if (e == cudaSuccess) {
+    b.mb->apply_rescale(b.stream, lc);
     for (int it = 0; it < ce; ++it) b.mb->iterate(b.stream, lc);
     b.mb->kkt(b.stream, lc);
     e = cudaGetLastError();
   }
+  b.mb->clear_rescale();   // the launched period applied the factors the device holds
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b.h_red, b.mb->red_out(), sizeof(double) * (size_t)b.G * R_NSLOTS, cudaMemcpyDeviceToHost,
                         b.stream);
@@ -352,7 +355,7 @@ void dot_server::finish_period(Batch& b) {
       r->sigma *= opt.s_sigma;
     else if (ratio < 1.0 / opt.s_r)
       r->sigma /= opt.s_sigma;
-    b.mb->set_sigma(k, r->sigma, opt.tau);
+    b.mb->set_sigma(k, r->sigma, opt.tau, true);
   }
 }
 

@@ -35,6 +35,8 @@ constexpr int kThreads = 256;
 constexpr int NQ1 = (TX + 1) * TY;       // x-faces per time node: j in [x0-1, x0+15], y owned
 constexpr int NQ2 = TX * (TY + 1);       // y-faces per time node: x owned, j in [y0-1, y0+31]
 
+// The multipliers are stored as alpha/sigma and beta/sigma (k_mixed.cu), so the
+// projection input is BFq + d - (stored beta) and the updates add tau (...).
 struct FusedArgs {
   // iteration k (read)
   const float* q[3];
@@ -46,8 +48,7 @@ struct FusedArgs {
   float2* betan;
   const float2* phi;   // phi^{k+1}
   const float* somega;
-  float2 isg;          // 1/sigma as a two-float (set per slot from sp)
-  float ts;            // tau * sigma (set per slot from sp)
+  float ts;            // tau (set per slot from sp)
   int tchunk;          // cone times per CTA
   int nchunk;          // time chunks per slot (grid z = slots x chunks)
   const SlotParam* sp;
@@ -59,8 +60,7 @@ struct FusedArgs {
 // The arguments of slot b of a batch.
 __device__ __forceinline__ FusedArgs fused_slot(FusedArgs a, const Geo& g, int b) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
-  a.isg = a.sp[b].isg;
-  a.ts = a.sp[b].ts;
+  a.ts = a.sp[b].tau;
   if (b == 0) return a;
   a.q[0] += b * n0;
   a.al[0] += b * n0;
@@ -123,11 +123,11 @@ __device__ __forceinline__ bool cone_z(const Geo& g, const FusedArgs& a, int t, 
   xv[7] = yl ? q2[i + P - 1] : 0.f;
   xv[8] = yr ? q2[i + P] : 0.f;
   const float s = a.somega ? a.somega[(long long)x * N1 + y] : 0.70710678118654752f;
-  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(ff_mul(a.beta[i], a.isg)));
+  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(a.beta[i]));
 #pragma unroll
   for (int j = 1; j < K2 - 1; ++j)
-    z[j] = ff_add(two_prod(s, xv[j]), ff_neg(ff_mul(a.beta[(long long)j * n0 + i], a.isg)));
-  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(ff_mul(a.beta[(long long)(K2 - 1) * n0 + i], a.isg)));
+    z[j] = ff_add(two_prod(s, xv[j]), ff_neg(a.beta[(long long)j * n0 + i]));
+  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(a.beta[(long long)(K2 - 1) * n0 + i]));
   ff_proj_soc<K2>(z);
   return true;
 }
@@ -153,7 +153,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) 
   const bool last_chunk = (tb == g.T);
   const long long P = g.P, n0 = (long long)g.T * P;
   const long long N1 = g.N[1];
-  const float2 isg = a.isg;
   const float ts = a.ts;
   const float ih0 = (float)g.invh[0], ih1 = (float)g.invh[1], ih2 = (float)g.invh[2];
   const float s_def = 0.70710678118654752f;
@@ -181,14 +180,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) 
         if (ok) {
           const long long i = (long long)t * P + (long long)x * N1 + y;
 #pragma unroll
-          for (int v = 0; v < 8; ++v) su[lev][v][hc] = ff_add(z[1 + v], ff_mul(a.beta[(long long)(1 + v) * n0 + i], isg));
+          for (int v = 0; v < 8; ++v) su[lev][v][hc] = ff_add(z[1 + v], a.beta[(long long)(1 + v) * n0 + i]);
           if (t >= ta && t < tb) {
             // lines 4-5 on q_0: rhs = A_0 phi + (alpha_0 + beta_{K-1} - beta_0)/sigma + (z_{K-1} - z_0),
             // diagonal 3, in two-float arithmetic
             const float2 gp = grad_pair(a.phi, i, i + P, ih0);
             const float2 al = a.al[0][i];
             const float2 db = ff_add(a.beta[(long long)(K2 - 1) * n0 + i], ff_neg(a.beta[i]));
-            float2 rhs = ff_add(gp, ff_mul(ff_add(al, db), isg));
+            float2 rhs = ff_add(gp, ff_add(al, db));
             rhs = ff_add(rhs, ff_add(z[K2 - 1], ff_neg(z[0])));
             const float qn = ff_round(ff_div_f(rhs, 3.f));
             a.qn[0][i] = qn;
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) 
         if (cone_z(g, a, t, x, y, z)) {
           const long long i = (long long)t * P + (long long)x * N1 + y;
 #pragma unroll
-          for (int v = 0; v < 8; ++v) su[lev][v][hc] = ff_add(z[1 + v], ff_mul(a.beta[(long long)(1 + v) * n0 + i], isg));
+          for (int v = 0; v < 8; ++v) su[lev][v][hc] = ff_add(z[1 + v], a.beta[(long long)(1 + v) * n0 + i]);
         } else {
 #pragma unroll
           for (int v = 0; v < 8; ++v) su[lev][v][hc] = make_float2(0.f, 0.f);
@@ -248,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) 
               dg += sr * sr + sl * sl;
             }
             const float2 al = a.al[1][i];
-            const float2 rhs = ff_add(ff_add(gp, ff_mul(al, isg)), acc);
+            const float2 rhs = ff_add(ff_add(gp, al), acc);
             qv = ff_round(ff_div_f(rhs, 1.f + dg));
             if (write_node && jx >= 1) {
               a.qn[1][i] = qv;
@@ -280,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) 
               dg += sr * sr + sl * sl;
             }
             const float2 al = a.al[2][i];
-            const float2 rhs = ff_add(ff_add(gp, ff_mul(al, isg)), acc);
+            const float2 rhs = ff_add(ff_add(gp, al), acc);
             qv = ff_round(ff_div_f(rhs, 1.f + dg));
             if (write_node && jy >= 1) {
               a.qn[2][i] = qv;
@@ -378,7 +377,6 @@ void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, 
   a.betan = fn.beta;
   a.phi = f.phi;
   a.somega = f.somega;
-  a.isg = make_float2(0.f, 0.f);
   a.ts = 0.f;
   a.tchunk = g.T <= 16 ? g.T : 16;
   a.nchunk = (g.T + a.tchunk - 1) / a.tchunk;
@@ -481,10 +479,10 @@ __device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, co
   xv[7] = yl ? q2[i + P - 1] : 0.f;
   xv[8] = yr ? q2[i + P] : 0.f;
   const float s = a.somega ? a.somega[x * N1 + y] : 0.70710678118654752f;
-  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(ff_mul(bt(tile, 0, xh, yh), a.isg)));
+  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(bt(tile, 0, xh, yh)));
 #pragma unroll
-  for (int j = 1; j < K2 - 1; ++j) z[j] = ff_add(two_prod(s, xv[j]), ff_neg(ff_mul(bt(tile, j, xh, yh), a.isg)));
-  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(ff_mul(bt(tile, K2 - 1, xh, yh), a.isg)));
+  for (int j = 1; j < K2 - 1; ++j) z[j] = ff_add(two_prod(s, xv[j]), ff_neg(bt(tile, j, xh, yh)));
+  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(bt(tile, K2 - 1, xh, yh)));
   ff_proj_soc<K2>(z);
   return true;
 }
@@ -508,7 +506,6 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
   const int tb = min(g.T, ta + a.tchunk);
   const bool last_chunk = (tb == g.T);
   const int P = (int)g.P, n0 = g.T * P, N1 = g.N[1];
-  const float2 isg = a.isg;
   const float ts = a.ts;
   const float ih0 = (float)g.invh[0], ih1 = (float)g.invh[1], ih2 = (float)g.invh[2];
   const float s_def = 0.70710678118654752f;
@@ -567,7 +564,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
             const float2 gp = grad_pair(a.phi, i, i + P, ih0);
             const float2 al = a.al[0][i];
             const float2 db = ff_add(bt(tcur, K2 - 1, xh, yh), ff_neg(bt(tcur, 0, xh, yh)));
-            float2 rhs = ff_add(gp, ff_mul(ff_add(al, db), isg));
+            float2 rhs = ff_add(gp, ff_add(al, db));
             rhs = ff_add(rhs, ff_add(z[K2 - 1], ff_neg(z[0])));
             const float qn = ff_round(ff_div_f(rhs, 3.f));
             a.qn[0][i] = qn;
@@ -627,7 +624,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
               zs += sr * zt[lp][2][xr * VHY + yh] + sl * zt[lp][3][xl * VHY + yh];
               dg += sr * sr + sl * sl;
             }
-            const float2 rhs = ff_add_f(ff_add(gp, ff_mul(mb, isg)), zs);
+            const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
             qv = ff_round(ff_div_f(rhs, 1.f + dg));
             if (write_node && jx >= 1) {
               a.qn[1][i] = qv;
@@ -658,7 +655,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
               zs += sr * zt[lp][6][xh * VHY + yr] + sl * zt[lp][7][xh * VHY + yl];
               dg += sr * sr + sl * sl;
             }
-            const float2 rhs = ff_add_f(ff_add(gp, ff_mul(mb, isg)), zs);
+            const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
             qv = ff_round(ff_div_f(rhs, 1.f + dg));
             if (write_node && jy >= 1) {
               a.qn[2][i] = qv;
@@ -755,7 +752,6 @@ bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& 
   a.betan = fn.beta;
   a.phi = f.phi;
   a.somega = f.somega;
-  a.isg = make_float2(0.f, 0.f);
   a.ts = 0.f;
   a.tchunk = g.T <= 16 ? g.T : 16;
   a.nchunk = (g.T + a.tchunk - 1) / a.tchunk;

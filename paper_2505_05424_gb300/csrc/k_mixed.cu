@@ -1,8 +1,11 @@
 // k_mixed.cu -- mixed-precision kernels of Algorithm 2 (lines 1, 3, 4, 5, 6),
 // the exact-residual step of the Poisson refinement, and the stopping measures.
 //
-// Storage: q and z in FP32; alpha, beta and phi as two-float pairs (hi, lo);
-// b and the Poisson scratch in FP32.  Arithmetic is FP32; updates of the
+// Storage: q and z in FP32; the multipliers as alpha/sigma and beta/sigma and
+// the potential phi as two-float pairs (hi, lo); the Poisson scratch in FP32.
+// With the multipliers stored divided by sigma, every alpha/sigma and beta/sigma
+// of Algorithm 2 is a load, the updates alpha += tau sigma (...) become
+// alpha/sigma += tau (...), and a penalty change rescales the stored values once.  Arithmetic is FP32; updates of the
 // two-float fields use error-free transformations (ffloat.cuh); the reduction
 // tree of the stopping measures is FP64.  Kernels are templated on D so the cone
 // (K = 4D + 2 components) lives in registers.
@@ -178,12 +181,12 @@ __global__ void k_assemble_residual(Geo g, MxFields fb) {
     {
       float2 sd = make_float2(0.f, 0.f);
       if (t >= 1) {
-        const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i - g.P], isg)), f.q[0][i - g.P]);
+        const float2 w = ff_add_f(ff_neg(f.al[0][i - g.P]), f.q[0][i - g.P]);
         acc = ff_add(acc, ff_mul_f(w, ih0));
         sd = ff_add(sd, ff_diff(xi, x[i - g.P]));
       }
       if (t < g.T) {
-        const float2 w = ff_add_f(ff_neg(ff_mul(f.al[0][i], isg)), f.q[0][i]);
+        const float2 w = ff_add_f(ff_neg(f.al[0][i]), f.q[0][i]);
         acc = ff_add(acc, ff_neg(ff_mul_f(w, ih0)));
         sd = ff_add(sd, ff_diff(xi, x[i + g.P]));
       }
@@ -198,12 +201,12 @@ __global__ void k_assemble_residual(Geo g, MxFields fb) {
       const float ih = (float)g.invh[1 + d];
       float2 sd = make_float2(0.f, 0.f);
       if (xd >= 1) {
-        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i - s], isg)), qd[i - s]);
+        const float2 w = ff_add_f(ff_neg(ad[i - s]), qd[i - s]);
         acc = ff_add(acc, ff_mul_f(w, ih));
         sd = ff_add(sd, ff_diff(xi, x[i - s]));
       }
       if (xd <= g.N[d] - 2) {
-        const float2 w = ff_add_f(ff_neg(ff_mul(ad[i], isg)), qd[i]);
+        const float2 w = ff_add_f(ff_neg(ad[i]), qd[i]);
         acc = ff_add(acc, ff_neg(ff_mul_f(w, ih)));
         sd = ff_add(sd, ff_diff(xi, x[i + s]));
       }
@@ -214,6 +217,24 @@ __global__ void k_assemble_residual(Geo g, MxFields fb) {
     const float2 r = ff_add(acc, ff_neg(lap));
     f.r[i] = r.x + r.y;
   }
+}
+
+// After a penalty change sigma_old -> sigma_new: alpha/sigma and beta/sigma of the
+// current set times sigma_old / sigma_new (two-float).
+template <int D>
+__global__ void k_rescale(Geo g, MxFields fb) {
+  const int slot = blockIdx.y;
+  const SlotParam sp = fb.sp[slot];
+  if (!sp.active || (sp.rescale.x == 1.f && sp.rescale.y == 0.f)) return;
+  const MxFields f = slot_view(fb, g, slot);
+  const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long i = i0; i < n0; i += stride) f.al[0][i] = ff_mul(f.al[0][i], sp.rescale);
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    for (long long i = i0; i < nn; i += stride) f.al[1 + d][i] = ff_mul(f.al[1 + d][i], sp.rescale);
+  for (long long i = i0; i < (long long)g.K * n0; i += stride) f.beta[i] = ff_mul(f.beta[i], sp.rescale);
 }
 
 // phi^{k+1} = phi^k + delta (delta in phi1).
@@ -264,7 +285,6 @@ template <int D>
 __global__ void k_project(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
-  const float2 isg = fb.sp[slot].isg;
   const MxFields f = slot_view(fb, g, slot);
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
@@ -276,10 +296,10 @@ __global__ void k_project(Geo g, MxFields fb) {
     gather_Fq<D>(g, f.q, i, p, x);
     const float s = f.somega ? f.somega[p] : s_default;
     float2 y[K];
-    y[0] = ff_add(two_sum(-x[0], 1.f), ff_neg(ff_mul(f.beta[i], isg)));
+    y[0] = ff_add(two_sum(-x[0], 1.f), ff_neg(f.beta[i]));
 #pragma unroll
-    for (int j = 1; j < K - 1; ++j) y[j] = ff_add(two_prod(s, x[j]), ff_neg(ff_mul(f.beta[(long long)j * n0 + i], isg)));
-    y[K - 1] = ff_add(two_sum(x[0], 1.f), ff_neg(ff_mul(f.beta[(long long)(K - 1) * n0 + i], isg)));
+    for (int j = 1; j < K - 1; ++j) y[j] = ff_add(two_prod(s, x[j]), ff_neg(f.beta[(long long)j * n0 + i]));
+    y[K - 1] = ff_add(two_sum(x[0], 1.f), ff_neg(f.beta[(long long)(K - 1) * n0 + i]));
     ff_proj_soc<K>(y);
 #pragma unroll
     for (int j = 0; j < K; ++j) f.z[(long long)j * n0 + i] = ff_round(y[j]);
@@ -292,8 +312,7 @@ template <int D>
 __global__ void k_update_q0(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
-  const float2 isg = fb.sp[slot].isg;
-  const float ts = fb.sp[slot].ts;
+  const float ts = fb.sp[slot].tau;
   const MxFields f = slot_view(fb, g, slot);
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
@@ -304,7 +323,7 @@ __global__ void k_update_q0(Geo g, MxFields fb) {
     const long long oK = (long long)(K - 1) * n0 + i;
     // u_{K-1} - u_0 = (z_{K-1} - z_0) + (beta_{K-1} - beta_0)/sigma
     const float2 db = ff_add(f.beta[oK], ff_neg(f.beta[i]));
-    float2 rhs = ff_add(gp, ff_mul(ff_add(f.al[0][i], db), isg));
+    float2 rhs = ff_add(gp, ff_add(f.al[0][i], db));
     rhs = ff_add_f(rhs, f.z[oK] - f.z[i]);
     const float qn = ff_round(ff_div_f(rhs, 3.f));
     f.q[0][i] = qn;
@@ -319,8 +338,7 @@ template <int D>
 __global__ void k_update_qd(Geo g, MxFields fb, int d) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
-  const float2 isg = fb.sp[slot].isg;
-  const float ts = fb.sp[slot].ts;
+  const float ts = fb.sp[slot].tau;
   const MxFields f = slot_view(fb, g, slot);
   const long long n = (long long)(g.T + 1) * g.P;
   const long long n0 = (long long)g.T * g.P;
@@ -355,7 +373,7 @@ __global__ void k_update_qd(Geo g, MxFields fb, int d) {
       zs += s_r * f.z[o3] + s_l * f.z[o4];
       dg += s_r * s_r + s_l * s_l;
     }
-    const float2 rhs = ff_add_f(ff_add(gp, ff_mul(mb, isg)), zs);
+    const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
     const float qn = ff_round(ff_div_f(rhs, 1.f + dg));
     qd[i] = qn;
     ad[i] = ff_add_f(ad[i], ts * grad_minus(gp, qn));
@@ -367,7 +385,7 @@ template <int D>
 __global__ void k_update_beta(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
-  const float ts = fb.sp[slot].ts;
+  const float ts = fb.sp[slot].tau;
   const MxFields f = slot_view(fb, g, slot);
   constexpr int K = 4 * D + 2;
   const long long n0 = (long long)g.T * g.P;
@@ -427,6 +445,7 @@ __global__ void k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z)
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
+  const float sg = fb.sp[slot].sg.x + fb.sp[slot].sg.y;
   double* partials = partials_all + slot * kkt_partials_len_slot(g);
   constexpr int K = 4 * D + 2;
   float acc[R_NSLOTS];
@@ -452,7 +471,7 @@ __global__ void k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z)
     for (int j = 1; j < K - 1; ++j) ss += x[j] * x[j];
     const float om = f.omega ? f.omega[p] : 1.f;
     const float fv = q0 + 0.125f * om * ss;
-    const float a0 = f.al[0][i].x + f.al[0][i].y;
+    const float a0 = sg * (f.al[0][i].x + f.al[0][i].y);
     const float m = fv + a0;
     const float rc = a0 - (m > 0.f ? m : 0.f);
     acc[R_COMP0] += rc * rc;
@@ -471,7 +490,7 @@ __global__ void k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z)
       acc[R_SOCP] += r * r;
     }
     const float2 bK = f.beta[(long long)(K - 1) * n0 + i], b0 = f.beta[i];
-    const float fbb = (bK.x - b0.x) + (bK.y - b0.y);
+    const float fbb = sg * ((bK.x - b0.x) + (bK.y - b0.y));
     acc[R_SOCD] += (fbb + a0) * (fbb + a0);
     acc[R_FBB] += fbb * fbb;
   }
@@ -483,6 +502,7 @@ __global__ void k_kkt_faces(Geo g, MxFields fb, int d, double* partials_all) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
+  const float sg = fb.sp[slot].sg.x + fb.sp[slot].sg.y;
   double* partials = partials_all + slot * kkt_partials_len_slot(g) + (long long)(1 + d) * kKktBlocks * R_NSLOTS;
   float acc[R_NSLOTS];
   double accd[R_NSLOTS];
@@ -522,9 +542,10 @@ __global__ void k_kkt_faces(Geo g, MxFields fb, int d, double* partials_all) {
       fbb += s_r * f.beta[(long long)(cbase + 2) * n0 + i - g.P + s].x +
              s_l * f.beta[(long long)(cbase + 3) * n0 + i - g.P].x;
     }
-    den *= 0.25f;
+    den *= 0.25f * sg;
+    fbb *= sg;
     const float gv = den * q;
-    const float a = ad[i].x + ad[i].y;
+    const float a = sg * (ad[i].x + ad[i].y);
     acc[R_COMPD] += (a - gv) * (a - gv);
     acc[R_ALPHAB] += a * a;
     acc[R_G] += gv * gv;
@@ -545,6 +566,7 @@ __global__ void k_kkt_nodes(Geo g, MxFields fb, double* partials_all) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
+  const float2 sg2 = fb.sp[slot].sg;
   double* partials = partials_all + slot * kkt_partials_len_slot(g) + (long long)(1 + D) * kKktBlocks * R_NSLOTS;
   float acc[R_NSLOTS];
   double accd[R_NSLOTS];
@@ -567,6 +589,7 @@ __global__ void k_kkt_nodes(Geo g, MxFields fb, double* partials_all) {
       if (x >= 1) v = ff_add(v, ff_mul_f(ad[i - s], ih));
       if (x <= g.N[d] - 2) v = ff_add(v, ff_mul_f(ff_neg(ad[i]), ih));
     }
+    v = ff_mul(v, sg2);   // A^* alpha = sigma A^*(alpha / sigma)
     double c = 0.0;
     if (t == 0) c += f.m0[p];
     if (t == g.T) c -= f.m1[p];
@@ -691,6 +714,13 @@ void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxP
                                bool have_bsum, cudaStream_t s, LaunchCounter lc) {
   if (g.D == 2) poisson_refined_tmpl<2>(g, G, f, ps, out, have_bsum, s, lc);
   else poisson_refined_tmpl<3>(g, G, f, ps, out, have_bsum, s, lc);
+}
+
+void launch_rescale_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc) {
+  const long long nb = (long long)g.K * g.T * g.P;
+  if (g.D == 2) k_rescale<2><<<dim3(grid_for(nb), G), kThreads, 0, s>>>(g, f);
+  else k_rescale<3><<<dim3(grid_for(nb), G), kThreads, 0, s>>>(g, f);
+  lc.launched(KID_UPDATE_BETA);
 }
 
 void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,

@@ -159,7 +159,7 @@ class PathF64 : public Path {
     return DOT_OK;
   }
 
-  int write_state(const double* q, const double* al, const double* beta, cudaStream_t s,
+  int write_state(const double* q, const double* al, const double* beta, double /*sigma*/, cudaStream_t s,
                   std::string* err) override {
     cudaError_t e = zero_iterate(s);
     if (e == cudaSuccess) e = write_faces(q, B_.f.q, s);

@@ -121,7 +121,9 @@ cudaError_t down(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 MixedBatch::MixedBatch(const Geo& g, int G, bool slot_masks)
     : g_(g), G_(G), slot_masks_(slot_masks), B_(new Buffers()) {
   std::memset(&ps_, 0, sizeof(ps_));
-  hp_.assign(G, SlotParam{make_float2(0.f, 0.f), 0.f, 0});
+  const SlotParam empty{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(1.f, 0.f), 0.f, 0};
+  hp_.assign(G, empty);
+  hs_.assign(G, 0.0);
 }
 
 MixedBatch::~MixedBatch() {}
@@ -244,7 +246,10 @@ int MixedBatch::init(char* ws, size_t bytes, cudaStream_t s, std::string* err) {
   if (e == cudaSuccess) e = cudaMemsetAsync(B.f.phi1, 0, (size_t)G_ * nn * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.f.r, 0, (size_t)G_ * nn * 4, s);
   for (int b = 0; b < G_ && e == cudaSuccess; ++b) e = zero_slot(b, s);
-  for (int b = 0; b < G_; ++b) hp_[b] = SlotParam{make_float2(0.f, 0.f), 0.f, 0};
+  for (int b = 0; b < G_; ++b) {
+    hp_[b] = SlotParam{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(1.f, 0.f), 0.f, 0};
+    hs_[b] = 0.0;
+  }
   if (e == cudaSuccess) e = upload_params(s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { *err = std::string("init: ") + cudaGetErrorString(e); return DOT_ECUDA; }
@@ -306,16 +311,37 @@ int MixedBatch::load_slot(int b, const std::vector<double>& m0, const std::vecto
     }
   }
   if (e == cudaSuccess) e = zero_slot(b, s);
-  set_sigma(b, sigma, tau);
+  set_sigma(b, sigma, tau, false);
   hp_[b].active = 1;
   if (e == cudaSuccess) e = upload_params(s);
   if (e != cudaSuccess) { *err = std::string("load_slot: ") + cudaGetErrorString(e); return DOT_ECUDA; }
   return DOT_OK;
 }
 
-void MixedBatch::set_sigma(int b, double sigma, double tau) {
+void MixedBatch::set_sigma(int b, double sigma, double tau, bool rescale) {
+  if (rescale && hs_[b] > 0.0 && sigma != hs_[b]) {
+    // compose with a factor not yet applied
+    const double pending = (double)hp_[b].rescale.x + (double)hp_[b].rescale.y;
+    hp_[b].rescale = split_ff(pending * hs_[b] / sigma);
+  } else if (!rescale) {
+    hp_[b].rescale = make_float2(1.f, 0.f);
+  }
   hp_[b].isg = split_ff(1.0 / sigma);
-  hp_[b].ts = (float)(tau * sigma);
+  hp_[b].sg = split_ff(sigma);
+  hp_[b].tau = (float)tau;
+  hs_[b] = sigma;
+}
+
+bool MixedBatch::rescale_pending() const {
+  for (const SlotParam& p : hp_)
+    if (p.active && !(p.rescale.x == 1.f && p.rescale.y == 0.f)) return true;
+  return false;
+}
+
+void MixedBatch::apply_rescale(cudaStream_t s, LaunchCounter lc) { launch_rescale_mx(g_, G_, cur(), s, lc); }
+
+void MixedBatch::clear_rescale() {
+  for (SlotParam& p : hp_) p.rescale = make_float2(1.f, 0.f);
 }
 
 void MixedBatch::set_active(int b, bool on) { hp_[b].active = on ? 1 : 0; }
@@ -365,12 +391,12 @@ cudaError_t face_ff_d2h(const Geo& g, int fam, const float2* src, double* dst, c
   return e;
 }
 cudaError_t face_h2d(const Geo& g, int fam, float* qd, float2* ad, const double* q, const double* al,
-                     cudaStream_t s) {
+                     double ascale, cudaStream_t s) {
   size_t w, p, h;
   face_copy_shape(g, fam, &w, &p, &h);
   std::vector<float> tq(w * h);
   std::vector<float2> ta(w * h);
-  for (size_t i = 0; i < w * h; ++i) { tq[i] = (float)q[i]; ta[i] = split_ff(al[i]); }
+  for (size_t i = 0; i < w * h; ++i) { tq[i] = (float)q[i]; ta[i] = split_ff(al[i] * ascale); }
   cudaError_t e = cudaMemcpy2DAsync(qd, p * 4, tq.data(), w * 4, w * 4, h, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpy2DAsync(ad, p * 8, ta.data(), w * 8, w * 8, h, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -383,17 +409,20 @@ int MixedBatch::read_fields(int b, double* rho, double* m, double* phi, cudaStre
   cudaError_t e = cudaSuccess;
   const size_t n0 = (size_t)g_.T * g_.P, nn = (size_t)(g_.T + 1) * g_.P;
   const MxFields fc = slot_view(cur(), g_, b);
+  const double sig = hs_[b];   // the stored multipliers are alpha / sigma
   if (rho) {
     std::vector<float2> t(n0);
     e = down(t.data(), fc.al[0], n0 * 8, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (size_t i = 0; i < n0; ++i) rho[i] = (double)t[i].x + (double)t[i].y;
+    for (size_t i = 0; i < n0; ++i) rho[i] = sig * ((double)t[i].x + (double)t[i].y);
   }
   if (m && e == cudaSuccess) {
     double* dst = m;
     for (int fam = 1; fam <= g_.D && e == cudaSuccess; ++fam) {
       e = face_ff_d2h(g_, fam, fc.al[fam], dst, s);
-      dst += natural_face_count(g_, fam);
+      const long long n = natural_face_count(g_, fam);
+      for (long long i = 0; i < n; ++i) dst[i] *= sig;
+      dst += n;
     }
   }
   if (phi && e == cudaSuccess) {
@@ -421,15 +450,18 @@ int MixedBatch::read_state(int b, double* q, double* al, double* beta, cudaStrea
       dst += natural_face_count(g_, fam);
     }
   }
+  const double sig = hs_[b];   // the stored multipliers are alpha / sigma, beta / sigma
   if (al && e == cudaSuccess) {
     std::vector<float2> t(n0);
     e = down(t.data(), fc.al[0], n0 * 8, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (size_t i = 0; i < n0; ++i) al[i] = (double)t[i].x + (double)t[i].y;
+    for (size_t i = 0; i < n0; ++i) al[i] = sig * ((double)t[i].x + (double)t[i].y);
     double* dst = al + n0;
     for (int fam = 1; fam <= g_.D && e == cudaSuccess; ++fam) {
       e = face_ff_d2h(g_, fam, fc.al[fam], dst, s);
-      dst += natural_face_count(g_, fam);
+      const long long n = natural_face_count(g_, fam);
+      for (long long i = 0; i < n; ++i) dst[i] *= sig;
+      dst += n;
     }
   }
   if (beta && e == cudaSuccess) {
@@ -437,34 +469,37 @@ int MixedBatch::read_state(int b, double* q, double* al, double* beta, cudaStrea
     std::vector<float2> t(nb);
     e = down(t.data(), fc.beta, nb * 8, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (size_t i = 0; i < nb; ++i) beta[i] = (double)t[i].x + (double)t[i].y;
+    for (size_t i = 0; i < nb; ++i) beta[i] = sig * ((double)t[i].x + (double)t[i].y);
   }
   if (e != cudaSuccess) { *err = std::string("read_state: ") + cudaGetErrorString(e); return DOT_ECUDA; }
   return DOT_OK;
 }
 
-int MixedBatch::write_state(int b, const double* q, const double* al, const double* beta, cudaStream_t s,
-                            std::string* err) {
+int MixedBatch::write_state(int b, const double* q, const double* al, const double* beta, double sigma,
+                            double tau, cudaStream_t s, std::string* err) {
   cudaError_t e = zero_slot(b, s);
-  // both sets were zeroed; write into the current one
+  // both sets were zeroed; write into the current one, the multipliers divided by sigma
+  set_sigma(b, sigma, tau, false);
+  if (e == cudaSuccess) e = upload_params(s);
+  const double is = 1.0 / sigma;
   const MxFields fc = slot_view(cur(), g_, b);
   const size_t n0 = (size_t)g_.T * g_.P;
   std::vector<float> tq(n0);
   std::vector<float2> ta(n0);
-  for (size_t i = 0; i < n0; ++i) { tq[i] = (float)q[i]; ta[i] = split_ff(al[i]); }
+  for (size_t i = 0; i < n0; ++i) { tq[i] = (float)q[i]; ta[i] = split_ff(al[i] * is); }
   if (e == cudaSuccess) e = up(fc.q[0], tq.data(), n0 * 4, s);
   if (e == cudaSuccess) e = up(fc.al[0], ta.data(), n0 * 8, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   const double* sq = q + n0;
   const double* sa = al + n0;
   for (int fam = 1; fam <= g_.D && e == cudaSuccess; ++fam) {
-    e = face_h2d(g_, fam, fc.q[fam], fc.al[fam], sq, sa, s);
+    e = face_h2d(g_, fam, fc.q[fam], fc.al[fam], sq, sa, is, s);
     sq += natural_face_count(g_, fam);
     sa += natural_face_count(g_, fam);
   }
   const size_t nb = (size_t)g_.K * n0;
   std::vector<float2> tb(nb);
-  for (size_t i = 0; i < nb; ++i) tb[i] = split_ff(beta[i]);
+  for (size_t i = 0; i < nb; ++i) tb[i] = split_ff(beta[i] * is);
   if (e == cudaSuccess) e = up(fc.beta, tb.data(), nb * 8, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { *err = std::string("write_state: ") + cudaGetErrorString(e); return DOT_ECUDA; }
@@ -524,8 +559,13 @@ class PathMixed : public Path {
     if (sigma != sigma_ || tau != tau_) {
       sigma_ = sigma;
       tau_ = tau;
-      batch_.set_sigma(0, sigma, tau);
+      batch_.set_sigma(0, sigma, tau, true);
       batch_.upload_params(s);
+      if (batch_.rescale_pending()) {
+        batch_.apply_rescale(s, lc);
+        batch_.clear_rescale();
+        batch_.upload_params(s);
+      }
     }
     batch_.iterate(s, lc);
   }
@@ -539,9 +579,10 @@ class PathMixed : public Path {
   int read_state(double* q, double* al, double* beta, cudaStream_t s, std::string* err) override {
     return batch_.read_state(0, q, al, beta, s, err);
   }
-  int write_state(const double* q, const double* al, const double* beta, cudaStream_t s,
+  int write_state(const double* q, const double* al, const double* beta, double sigma, cudaStream_t s,
                   std::string* err) override {
-    return batch_.write_state(0, q, al, beta, s, err);
+    sigma_ = sigma;
+    return batch_.write_state(0, q, al, beta, sigma, tau_, s, err);
   }
   int poisson_op(const double* b, double* phi, cudaStream_t s, LaunchCounter lc, std::string* err) override {
     return batch_.poisson_op(b, phi, s, lc, err);
