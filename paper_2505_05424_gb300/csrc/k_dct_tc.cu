@@ -169,7 +169,7 @@ struct PassArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(kThreadsTC, 1)
+__global__ void __launch_bounds__(kThreadsTC, 2)
 k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_bhi,
               const __grid_constant__ CUtensorMap tm_blo, PassArgs pa) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];

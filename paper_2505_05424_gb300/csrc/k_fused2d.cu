@@ -23,6 +23,10 @@
 #include "dot_tc.cuh"
 #include "ffloat.cuh"
 
+#ifndef FUSED_V2_MIN_BLOCKS
+#define FUSED_V2_MIN_BLOCKS 2
+#endif
+
 namespace dot {
 namespace {
 
@@ -423,6 +427,10 @@ constexpr int kOffQ2 = kOffQ1 + 2 * VNQ1 * 4;            // [2][VNQ2] floats
 constexpr int kOffBar = (kOffQ2 + 2 * VNQ2 * 4 + 15) / 16 * 16;
 constexpr int kSmemV2 = kOffBar + 64;
 constexpr unsigned kSpinV2 = 1u << 25;
+// 11 warps: one thread per cone of the 10 x 34 halo rectangle (256 owned + 84
+// ring cones), so phase A takes one round; 552 faces take two
+constexpr int kThreadsV2 = 352;
+constexpr int kMinBlocksV2 = FUSED_V2_MIN_BLOCKS;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -487,7 +495,7 @@ __device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, co
   return true;
 }
 
-__global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ CUtensorMap tmb, Geo g,
+__global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const __grid_constant__ CUtensorMap tmb, Geo g,
                                                         FusedArgs a_in) {
   const int slot = blockIdx.z / a_in.nchunk, chunk = blockIdx.z - slot * a_in.nchunk;
   if (!a_in.sp[slot].active) return;
@@ -500,6 +508,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
 
   const int tid = threadIdx.x;
+  const bool owner = tid < VX * VY;             // threads 0..255 own a cone column
   const int ly = tid & 31, lx = tid >> 5;       // owned node (x0 + lx, y0 + ly)
   const int x0 = blockIdx.x * VX, y0 = blockIdx.y * VY;
   const int ta = chunk * a.tchunk;
@@ -510,7 +519,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
   const float ih0 = (float)g.invh[0], ih1 = (float)g.invh[1], ih2 = (float)g.invh[2];
   const float s_def = 0.70710678118654752f;
   const int xo = x0 + lx, yo = y0 + ly;
-  const bool own_ok = xo < g.N[0] && yo < g.N[1];
+  const bool own_ok = owner && xo < g.N[0] && yo < g.N[1];
   const int tstart = ta > 0 ? ta - 1 : 0;
   const int tlast_cone = min(tb, g.T - 1);      // last cone time whose beta tile is loaded
 
@@ -553,7 +562,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
     }
     // ---------------- A: cones at time t ----------------
     if (t <= g.T - 1) {
-      {
+      if (owner) {
         const int xh = lx + 1, yh = ly + 1, hc = xh * VHY + yh;
         float2 z[K2];
         if (own_ok && cone_z_tile(g, a, tcur, t, xo, yo, xh, yh, z)) {
@@ -578,9 +587,9 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
           for (int v = 0; v < 8; ++v) zt[lev][v][hc] = 0.f;
         }
       }
-      // the 84 halo-ring cones
-      if (tid < VNH - VX * VY) {
-        int r = tid, xh, yh;
+      // the 84 halo-ring cones, one per thread 256..339
+      else if (tid < VNH) {
+        int r = tid - VX * VY, xh, yh;
         if (r < VHY) { xh = 0; yh = r; }
         else if ((r -= VHY) < VHY) { xh = VHX - 1; yh = r; }
         else if ((r -= VHY) < VHX - 2) { xh = 1 + r; yh = 0; }
@@ -601,7 +610,7 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
     if (t >= ta) {
       const bool write_node = (t < tb) || (last_chunk && t == g.T);
       const bool has_now = t <= g.T - 1, has_prev = t >= 1;
-      for (int e = tid; e < VNQ1 + VNQ2; e += 256) {
+      for (int e = tid; e < VNQ1 + VNQ2; e += kThreadsV2) {
         if (e < VNQ1) {
           const int jx = e / VY, yy = e % VY;
           const int j = x0 - 1 + jx, y = y0 + yy;
@@ -716,12 +725,12 @@ __global__ void __launch_bounds__(256, 2) k_fused2d_tma(const __grid_constant__ 
   if (a.socp_part) {
     double v = (double)socp;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __shared__ double wsum[8];
+    __shared__ double wsum[kThreadsV2 / 32];
     if ((tid & 31) == 0) wsum[tid >> 5] = v;
     __syncthreads();
     if (tid == 0) {
       double b = 0.0;
-      for (int w = 0; w < 8; ++w) b += wsum[w];
+      for (int w = 0; w < kThreadsV2 / 32; ++w) b += wsum[w];
       a.socp_part[(chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = b;
     }
   }
@@ -773,7 +782,7 @@ bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& 
     attr = true;
   }
   dim3 grid((unsigned)((g.N[0] + VX - 1) / VX), (unsigned)((g.N[1] + VY - 1) / VY), (unsigned)(a.nchunk * G));
-  k_fused2d_tma<<<grid, 256, kSmemV2, s>>>(tm, g, a);
+  k_fused2d_tma<<<grid, kThreadsV2, kSmemV2, s>>>(tm, g, a);
   lc.launched(KID_FUSED);
   return true;
 }
