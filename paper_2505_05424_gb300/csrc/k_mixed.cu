@@ -163,7 +163,7 @@ __device__ __forceinline__ float2 ff_diff(float2 a, float2 b) {
 // equal masses make sum(b) vanish up to rounding (|sum b| ~ 1e-16 |c| / sigma),
 // and the solve drops the zero mode.
 template <int D>
-__global__ void k_assemble_residual(Geo g, MxFields fb) {
+__global__ void __launch_bounds__(kThreads, D == 2 ? 4 : 3) k_assemble_residual(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const float2 isg = fb.sp[slot].isg;
@@ -441,7 +441,7 @@ __device__ __forceinline__ void block_reduce_store(const float* accf, const doub
 }
 
 template <int D>
-__global__ void k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z) {
+__global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
@@ -498,7 +498,7 @@ __global__ void k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z)
 }
 
 template <int D>
-__global__ void k_kkt_faces(Geo g, MxFields fb, int d, double* partials_all) {
+__global__ void __launch_bounds__(kThreads, 3) k_kkt_faces(Geo g, MxFields fb, int d, double* partials_all) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
