@@ -176,8 +176,9 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
         "poisson_residual": 3 * 4 * nc,
         "poisson_combine": (4 + 4 + 8) * nc,
         "dct_scale": 2 * (8 if prec == "fp64" else 4) * nc,
-        # lines 3-6 fused: read q, alpha, beta (iteration k) and phi; write q, alpha, beta (k+1)
-        "fused_cone_update": 2 * (w + ws) * nq + 2 * ws * K * n0 + wf * nc,
+        # lines 3-6 fused: read q, alpha/sigma, beta/sigma (iteration k) and phi; write
+        # q, alpha/sigma, beta/sigma (k+1) and the next iteration's residual r (FP32)
+        "fused_cone_update": 2 * (w + ws) * nq + 2 * ws * K * n0 + wf * nc + w * nc,
     }
     return float(table.get(name, 0.0))
 

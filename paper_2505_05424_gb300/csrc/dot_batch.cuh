@@ -76,6 +76,7 @@ class MixedBatch {
   bool slot_masks_;
   bool fused_ = false, tma_ = false;
   int cur_ = 0;
+  bool r_valid_ = false;   // f.r holds the next iteration's residual (from the fused kernel)
   std::unique_ptr<Buffers> B_;
   MxPoisson ps_;
   double* red_ = nullptr;

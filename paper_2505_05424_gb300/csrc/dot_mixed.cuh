@@ -112,6 +112,10 @@ void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxP
 // Multiply the stored alpha/sigma and beta/sigma of every slot whose rescale
 // factor is not 1 by that factor (after a penalty change).
 void launch_rescale_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, LaunchCounter lc);
+// Line 2 from a residual already in f.r (written by the fused cone kernel of the
+// previous iteration): one solve, phi += delta.
+void launch_solve_residual_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                              LaunchCounter lc);
 // Lines 1-2 of an iteration: b-assembly fused with the warm-start residual
 // (b never stored), one solve, phi += delta.
 void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
@@ -137,8 +141,10 @@ void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, 
 // be built.
 bool fused2d_tma_supported(const Geo& g);
 long long fused2d_tma_blocks(const Geo& g);
+// residual: also write the next iteration's lines 1-2 residual into f.r (see
+// launch_solve_residual_mx).
 bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part, int* err,
-                        cudaStream_t s, LaunchCounter lc);
+                        bool residual, cudaStream_t s, LaunchCounter lc);
 // KKT partial-sum scratch (doubles) per slot.
 long long kkt_partials_len_mx(const Geo& g);
 

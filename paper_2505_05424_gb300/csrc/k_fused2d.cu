@@ -59,12 +59,19 @@ struct FusedArgs {
   double* socp_part;   // per-block sum of |z - B F q^{k+1} - d|^2, or nullptr
   long long socp_per_slot;
   int* err;            // set when a pipeline wait gave up
+  // TMA kernel only (nullable r): the next iteration's lines 1-2 residual
+  // r = A^*(q^{k+1} - alpha^{k+1}/sigma) - c/sigma - A^*A phi^{k+1} at every node
+  float* r;
+  const float2* c0;
+  const float2* c1;
+  float2 isg;          // 1/sigma (set per slot from sp)
 };
 
 // The arguments of slot b of a batch.
 __device__ __forceinline__ FusedArgs fused_slot(FusedArgs a, const Geo& g, int b) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
   a.ts = a.sp[b].tau;
+  a.isg = a.sp[b].isg;
   if (b == 0) return a;
   a.q[0] += b * n0;
   a.al[0] += b * n0;
@@ -81,6 +88,11 @@ __device__ __forceinline__ FusedArgs fused_slot(FusedArgs a, const Geo& g, int b
   a.phi += b * nn;
   if (a.somega) a.somega += b * g.P;
   if (a.socp_part) a.socp_part += b * a.socp_per_slot;
+  if (a.r) {
+    a.r += b * nn;
+    a.c0 += b * g.P;
+    a.c1 += b * g.P;
+  }
   return a;
 }
 
@@ -223,8 +235,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused2d(Geo g, FusedArgs a_in) 
     }
     __syncthreads();
     // ---------------- B: faces at time node t ----------------
+    const bool write_node = t >= ta && ((t < tb) || (last_chunk && t == g.T));
     if (t >= ta) {
-      const bool write_node = (t < tb) || (last_chunk && t == g.T);
       const bool has_now = t <= g.T - 1, has_prev = t >= 1;
       const int lp = lev ^ 1;
       for (int e = tid; e < NQ1 + NQ2; e += kThreads) {
@@ -388,6 +400,8 @@ void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, 
   a.socp_part = socp_part;
   a.socp_per_slot = fused2d_blocks(g);
   a.err = nullptr;
+  a.r = nullptr;
+  a.c0 = a.c1 = nullptr;
   dim3 grid((unsigned)((g.N[0] + TX - 1) / TX), (unsigned)((g.N[1] + TY - 1) / TY), (unsigned)(a.nchunk * G));
   static bool attr = false;
   if (!attr) {
@@ -421,11 +435,18 @@ constexpr int VNQ1 = (VX + 1) * VY;          // 288 x-faces: j in [x0-1, x0+7], 
 constexpr int VNQ2 = VX * (VY + 1);          // 264 y-faces: x owned, j in [y0-1, y0+31]
 constexpr int kBetaTile = K2 * VHX * VBW;    // 3600 two-floats = 28800 bytes
 constexpr int kBetaTileBytes = kBetaTile * 8;
-constexpr int kOffZ = 3 * kBetaTileBytes;                 // z tile: [2][8][VNH] floats
-constexpr int kOffQ1 = kOffZ + 2 * 8 * VNH * 4;          // [2][VNQ1] floats
-constexpr int kOffQ2 = kOffQ1 + 2 * VNQ1 * 4;            // [2][VNQ2] floats
-constexpr int kOffBar = (kOffQ2 + 2 * VNQ2 * 4 + 15) / 16 * 16;
+// z of the halo cones: components 1, 2, 5, 6 of cone time t (read by the faces of
+// node t) once, components 3, 4, 7, 8 (read by the faces of node t+1) for two
+// cone times
+constexpr int kOffZ = 3 * kBetaTileBytes;                 // ztn [4][VNH] floats
+constexpr int kOffZP = kOffZ + 4 * VNH * 4;               // ztp [2][4][VNH] floats
+constexpr int kOffQ1 = kOffZP + 2 * 4 * VNH * 4;          // [2][VNQ1] floats
+constexpr int kOffQ2 = kOffQ1 + 2 * VNQ1 * 4;             // [2][VNQ2] floats
+constexpr int kOffW1 = kOffQ2 + 2 * VNQ2 * 4;             // [VNQ1] two-float q - alpha/sigma
+constexpr int kOffW2 = kOffW1 + VNQ1 * 8;                 // [VNQ2] two-float
+constexpr int kOffBar = (kOffW2 + VNQ2 * 8 + 15) / 16 * 16;
 constexpr int kSmemV2 = kOffBar + 64;
+static_assert(kOffW1 % 16 == 0, "two-float face arrays are 16-byte aligned");
 constexpr unsigned kSpinV2 = 1u << 25;
 // 11 warps: one thread per cone of the 10 x 34 halo rectangle (256 owned + 84
 // ring cones), so phase A takes one round; 552 faces take two
@@ -466,6 +487,30 @@ __device__ __forceinline__ float2 bt(const float2* tile, int c, int xh, int yh) 
   return tile[(c * VHX + xh) * VBW + yh + 1];
 }
 
+// z components 1..8 of a halo cone into the tiles: 1, 2, 5, 6 -> ztn; 3, 4, 7, 8 -> ztp
+__device__ __forceinline__ void put_z(float (*ztn)[VNH], float (*ztp)[VNH], int hc, const float2* z) {
+  ztn[0][hc] = ff_round(z[1]);
+  ztn[1][hc] = ff_round(z[2]);
+  ztn[2][hc] = ff_round(z[5]);
+  ztn[3][hc] = ff_round(z[6]);
+  ztp[0][hc] = ff_round(z[3]);
+  ztp[1][hc] = ff_round(z[4]);
+  ztp[2][hc] = ff_round(z[7]);
+  ztp[3][hc] = ff_round(z[8]);
+}
+__device__ __forceinline__ void put_z0(float (*ztn)[VNH], float (*ztp)[VNH], int hc) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    ztn[v][hc] = 0.f;
+    ztp[v][hc] = 0.f;
+  }
+}
+// a - b of two two-float values, unnormalised
+__device__ __forceinline__ float2 ff_diff(float2 a, float2 b) {
+  const float2 d = two_sum(a.x, -b.x);
+  return make_float2(d.x, d.y + (a.y - b.y));
+}
+
 // z of cone (t, x, y) from the iteration-k q (global) and a beta tile, in two-float
 // arithmetic as cone_z; false for a cone outside the grid.
 __device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, const float2* tile, int t, int x,
@@ -502,9 +547,12 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
   const FusedArgs a = fused_slot(a_in, g, slot);
   extern __shared__ __align__(128) unsigned char sm[];
   float2* btiles = reinterpret_cast<float2*>(sm);
-  float (*zt)[8][VNH] = reinterpret_cast<float (*)[8][VNH]>(sm + kOffZ);
+  float (*ztn)[VNH] = reinterpret_cast<float (*)[VNH]>(sm + kOffZ);
+  float (*ztp)[4][VNH] = reinterpret_cast<float (*)[4][VNH]>(sm + kOffZP);
   float (*sq1)[VNQ1] = reinterpret_cast<float (*)[VNQ1]>(sm + kOffQ1);
   float (*sq2)[VNQ2] = reinterpret_cast<float (*)[VNQ2]>(sm + kOffQ2);
+  float2* sw1 = reinterpret_cast<float2*>(sm + kOffW1);
+  float2* sw2 = reinterpret_cast<float2*>(sm + kOffW2);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
 
   const int tid = threadIdx.x;
@@ -538,6 +586,7 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
 
   float zc[K2], zp[K2];
   float q0c = 0.f, q0p = 0.f, socp = 0.f;
+  float2 w0c = make_float2(0.f, 0.f), w0p = make_float2(0.f, 0.f);   // q_0 - alpha_0/sigma, cones t, t-1
   bool failed = false;
 
   for (int t = tstart; t <= tb; ++t) {
@@ -566,9 +615,9 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
         const int xh = lx + 1, yh = ly + 1, hc = xh * VHY + yh;
         float2 z[K2];
         if (own_ok && cone_z_tile(g, a, tcur, t, xo, yo, xh, yh, z)) {
-#pragma unroll
-          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = ff_round(z[1 + v]);
-          if (t >= ta && t < tb) {
+          put_z(ztn, ztp[lev], hc, z);
+          // the cone before the chunk (t = ta - 1) is updated for the residual only
+          if (t < tb) {
             const int i = t * P + xo * N1 + yo;
             const float2 gp = grad_pair(a.phi, i, i + P, ih0);
             const float2 al = a.al[0][i];
@@ -576,15 +625,18 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
             float2 rhs = ff_add(gp, ff_add(al, db));
             rhs = ff_add(rhs, ff_add(z[K2 - 1], ff_neg(z[0])));
             const float qn = ff_round(ff_div_f(rhs, 3.f));
-            a.qn[0][i] = qn;
-            a.aln[0][i] = ff_add_f(al, ts * grad_minus(gp, qn));
+            const float2 aln = ff_add_f(al, ts * grad_minus(gp, qn));
+            if (t >= ta) {
+              a.qn[0][i] = qn;
+              a.aln[0][i] = aln;
+            }
             q0c = qn;
+            w0c = ff_add_f(ff_neg(aln), qn);
           }
 #pragma unroll
           for (int j = 0; j < K2; ++j) zc[j] = ff_round(z[j]);
         } else {
-#pragma unroll
-          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = 0.f;
+          put_z0(ztn, ztp[lev], hc);
         }
       }
       // the 84 halo-ring cones, one per thread 256..339
@@ -596,25 +648,21 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
         else { r -= VHX - 2; xh = 1 + r; yh = VHY - 1; }
         const int hc = xh * VHY + yh;
         float2 z[K2];
-        if (cone_z_tile(g, a, tcur, t, x0 - 1 + xh, y0 - 1 + yh, xh, yh, z)) {
-#pragma unroll
-          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = ff_round(z[1 + v]);
-        } else {
-#pragma unroll
-          for (int v = 0; v < 8; ++v) zt[lev][v][hc] = 0.f;
-        }
+        if (cone_z_tile(g, a, tcur, t, x0 - 1 + xh, y0 - 1 + yh, xh, yh, z)) put_z(ztn, ztp[lev], hc, z);
+        else put_z0(ztn, ztp[lev], hc);
       }
     }
     __syncthreads();
     // ---------------- B: faces at time node t ----------------
+    const bool write_node = t >= ta && ((t < tb) || (last_chunk && t == g.T));
     if (t >= ta) {
-      const bool write_node = (t < tb) || (last_chunk && t == g.T);
       const bool has_now = t <= g.T - 1, has_prev = t >= 1;
       for (int e = tid; e < VNQ1 + VNQ2; e += kThreadsV2) {
         if (e < VNQ1) {
           const int jx = e / VY, yy = e % VY;
           const int j = x0 - 1 + jx, y = y0 + yy;
           float qv = 0.f;
+          float2 wv = make_float2(0.f, 0.f);
           if (j >= 0 && j <= g.N[0] - 2 && y < g.N[1]) {
             const int i = t * P + j * N1 + y;
             const float2 gp = grad_pair(a.phi, i, i + N1, ih1);
@@ -625,27 +673,31 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
             float zs = 0.f, dg = 0.f;
             if (has_now) {
               mb = ff_add(mb, ff_add(ff_mul_f(bt(tcur, 1, xr, yh), sr), ff_mul_f(bt(tcur, 2, xl, yh), sl)));
-              zs += sr * zt[lev][0][xr * VHY + yh] + sl * zt[lev][1][xl * VHY + yh];
+              zs += sr * ztn[0][xr * VHY + yh] + sl * ztn[1][xl * VHY + yh];
               dg += sr * sr + sl * sl;
             }
             if (has_prev) {
               mb = ff_add(mb, ff_add(ff_mul_f(bt(tprev, 3, xr, yh), sr), ff_mul_f(bt(tprev, 4, xl, yh), sl)));
-              zs += sr * zt[lp][2][xr * VHY + yh] + sl * zt[lp][3][xl * VHY + yh];
+              zs += sr * ztp[lp][0][xr * VHY + yh] + sl * ztp[lp][1][xl * VHY + yh];
               dg += sr * sr + sl * sl;
             }
             const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
             qv = ff_round(ff_div_f(rhs, 1.f + dg));
+            const float2 aln = ff_add_f(a.al[1][i], ts * grad_minus(gp, qv));
             if (write_node && jx >= 1) {
               a.qn[1][i] = qv;
-              a.aln[1][i] = ff_add_f(a.al[1][i], ts * grad_minus(gp, qv));
+              a.aln[1][i] = aln;
             }
+            wv = ff_add_f(ff_neg(aln), qv);
           }
           sq1[lev][e] = qv;
+          sw1[e] = wv;
         } else {
           const int f = e - VNQ1;
           const int xx = f / (VY + 1), jy = f % (VY + 1);
           const int x = x0 + xx, j = y0 - 1 + jy;
           float qv = 0.f;
+          float2 wv = make_float2(0.f, 0.f);
           if (x < g.N[0] && j >= 0 && j <= g.N[1] - 2) {
             const int i = t * P + x * N1 + j;
             const float2 gp = grad_pair(a.phi, i, i + 1, ih2);
@@ -656,22 +708,25 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
             float zs = 0.f, dg = 0.f;
             if (has_now) {
               mb = ff_add(mb, ff_add(ff_mul_f(bt(tcur, 5, xh, yr), sr), ff_mul_f(bt(tcur, 6, xh, yl), sl)));
-              zs += sr * zt[lev][4][xh * VHY + yr] + sl * zt[lev][5][xh * VHY + yl];
+              zs += sr * ztn[2][xh * VHY + yr] + sl * ztn[3][xh * VHY + yl];
               dg += sr * sr + sl * sl;
             }
             if (has_prev) {
               mb = ff_add(mb, ff_add(ff_mul_f(bt(tprev, 7, xh, yr), sr), ff_mul_f(bt(tprev, 8, xh, yl), sl)));
-              zs += sr * zt[lp][6][xh * VHY + yr] + sl * zt[lp][7][xh * VHY + yl];
+              zs += sr * ztp[lp][2][xh * VHY + yr] + sl * ztp[lp][3][xh * VHY + yl];
               dg += sr * sr + sl * sl;
             }
             const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
             qv = ff_round(ff_div_f(rhs, 1.f + dg));
+            const float2 aln = ff_add_f(a.al[2][i], ts * grad_minus(gp, qv));
             if (write_node && jy >= 1) {
               a.qn[2][i] = qv;
-              a.aln[2][i] = ff_add_f(a.al[2][i], ts * grad_minus(gp, qv));
+              a.aln[2][i] = aln;
             }
+            wv = ff_add_f(ff_neg(aln), qv);
           }
           sq2[lev][f] = qv;
+          sw2[f] = wv;
         }
       }
     }
@@ -705,12 +760,51 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
       socp = fmaf(inc, inc, socp);
       a.betan[(K2 - 1) * n0 + i] = ff_add_f(bt(tprev, K2 - 1, xh, yh), ts * inc);
     }
+    // the next iteration's residual at the owned node of time t
+    if (a.r && own_ok && write_node) {
+      const int i = t * P + xo * N1 + yo;
+      const int p = xo * N1 + yo;
+      float2 acc = make_float2(0.f, 0.f), lap = make_float2(0.f, 0.f);
+      const float2 xi = a.phi[i];
+      {
+        float2 sd = make_float2(0.f, 0.f);
+        if (t >= 1) {
+          acc = ff_add(acc, ff_mul_f(w0p, ih0));
+          sd = ff_add(sd, ff_diff(xi, a.phi[i - P]));
+        }
+        if (t < g.T) {
+          acc = ff_add(acc, ff_neg(ff_mul_f(w0c, ih0)));
+          sd = ff_add(sd, ff_diff(xi, a.phi[i + P]));
+        }
+        lap = ff_add(lap, ff_mul_f(sd, ih0 * ih0));
+      }
+      {
+        // x-faces j = xo - 1 (row lx) and j = xo (row lx + 1); zero beyond the walls
+        acc = ff_add(acc, ff_mul_f(ff_add(sw1[lx * VY + ly], ff_neg(sw1[(lx + 1) * VY + ly])), ih1));
+        float2 sd = make_float2(0.f, 0.f);
+        if (xo >= 1) sd = ff_add(sd, ff_diff(xi, a.phi[i - N1]));
+        if (xo <= g.N[0] - 2) sd = ff_add(sd, ff_diff(xi, a.phi[i + N1]));
+        lap = ff_add(lap, ff_mul_f(sd, ih1 * ih1));
+      }
+      {
+        acc = ff_add(acc, ff_mul_f(ff_add(sw2[lx * (VY + 1) + ly], ff_neg(sw2[lx * (VY + 1) + ly + 1])), ih2));
+        float2 sd = make_float2(0.f, 0.f);
+        if (yo >= 1) sd = ff_add(sd, ff_diff(xi, a.phi[i - 1]));
+        if (yo <= g.N[1] - 2) sd = ff_add(sd, ff_diff(xi, a.phi[i + 1]));
+        lap = ff_add(lap, ff_mul_f(sd, ih2 * ih2));
+      }
+      if (t == 0) acc = ff_add(acc, ff_neg(ff_mul(a.c0[p], a.isg)));
+      if (t == g.T) acc = ff_add(acc, ff_mul(a.c1[p], a.isg));
+      const float2 rr = ff_add(acc, ff_neg(lap));
+      a.r[i] = rr.x + rr.y;
+    }
     q0p = q0c;
+    w0p = w0c;
 #pragma unroll
     for (int j = 0; j < K2; ++j) zp[j] = zc[j];
-    // no barrier here: step A of t+1 writes only zt[lev of t+1] (read by step B of
-    // t, which every thread finished before step C) and registers; step B of t+1,
-    // which overwrites the faces step C reads, follows the barrier after A
+    // no barrier here: step A of t+1 writes only ztn and ztp[lev of t+1] (read by
+    // step B of t, which every thread finished before step C) and registers; step B
+    // of t+1, which overwrites the faces step C reads, follows the barrier after A
   }
   if (failed) {
     // a tile load did not complete in time: wait (bounded) for the loads this
@@ -749,7 +843,7 @@ long long fused2d_tma_blocks(const Geo& g) {
 }
 
 bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part, int* err,
-                        cudaStream_t s, LaunchCounter lc) {
+                        bool residual, cudaStream_t s, LaunchCounter lc) {
   FusedArgs a;
   for (int d = 0; d < 3; ++d) {
     a.q[d] = f.q[d];
@@ -768,6 +862,10 @@ bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& 
   a.socp_part = socp_part;
   a.socp_per_slot = fused2d_tma_blocks(g);
   a.err = err;
+  a.r = residual ? f.r : nullptr;
+  a.c0 = f.c0;
+  a.c1 = f.c1;
+  a.isg = make_float2(0.f, 0.f);
   // beta as a 5-D tensor of 8-byte elements: (y, x, t, component, slot)
   CUtensorMap tm;
   const cuuint64_t dims[5] = {(cuuint64_t)g.N[1], (cuuint64_t)g.N[0], (cuuint64_t)g.T, (cuuint64_t)K2,

@@ -723,6 +723,11 @@ void launch_rescale_mx(const Geo& g, int G, const MxFields& f, cudaStream_t s, L
   lc.launched(KID_UPDATE_BETA);
 }
 
+void launch_solve_residual_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
+                              LaunchCounter lc) {
+  poisson_add_tmpl(g, G, f, ps, s, lc);
+}
+
 void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
                               LaunchCounter lc) {
   if (g.D == 2) assemble_solve_tmpl<2>(g, G, f, ps, s, lc);

@@ -313,6 +313,7 @@ int MixedBatch::load_slot(int b, const std::vector<double>& m0, const std::vecto
   if (e == cudaSuccess) e = zero_slot(b, s);
   set_sigma(b, sigma, tau, false);
   hp_[b].active = 1;
+  r_valid_ = false;
   if (e == cudaSuccess) e = upload_params(s);
   if (e != cudaSuccess) { *err = std::string("load_slot: ") + cudaGetErrorString(e); return DOT_ECUDA; }
   return DOT_OK;
@@ -338,7 +339,10 @@ bool MixedBatch::rescale_pending() const {
   return false;
 }
 
-void MixedBatch::apply_rescale(cudaStream_t s, LaunchCounter lc) { launch_rescale_mx(g_, G_, cur(), s, lc); }
+void MixedBatch::apply_rescale(cudaStream_t s, LaunchCounter lc) {
+  launch_rescale_mx(g_, G_, cur(), s, lc);
+  r_valid_ = false;
+}
 
 void MixedBatch::clear_rescale() {
   for (SlotParam& p : hp_) p.rescale = make_float2(1.f, 0.f);
@@ -355,9 +359,14 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
   if (fused_) {
     const MxFields& fc = cur();
     const MxFields& fn = other();
-    launch_assemble_solve_mx(g_, G_, fc, ps_, s, lc);                       // lines 1-2 (warm-started)
-    if (!(tma_ && launch_fused2d_tma(g_, G_, fc, fn, B_->socp, B_->err, s, lc)))
-      launch_fused2d(g_, G_, fc, fn, B_->socp, s, lc);                       // lines 3-6
+    // lines 1-2: the residual is assembled here unless the previous iteration's
+    // fused kernel left it in f.r (it cannot after a stopping-measure check, where
+    // sigma may change, or after a state or slot change)
+    if (r_valid_) launch_solve_residual_mx(g_, G_, fc, ps_, s, lc);
+    else launch_assemble_solve_mx(g_, G_, fc, ps_, s, lc);
+    // lines 3-6 (the TMA kernel also leaves the next residual in f.r)
+    r_valid_ = tma_ && launch_fused2d_tma(g_, G_, fc, fn, B_->socp, B_->err, true, s, lc);
+    if (!r_valid_) launch_fused2d(g_, G_, fc, fn, B_->socp, s, lc);
     cur_ ^= 1;
   } else {
     launch_iterate_mx(g_, G_, B_->f, ps_, s, lc);
@@ -365,6 +374,7 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
 }
 
 void MixedBatch::kkt(cudaStream_t s, LaunchCounter lc) {
+  r_valid_ = false;   // sigma may change after a check: the next iteration assembles afresh
   launch_kkt_mx(g_, G_, cur(), B_->partials, B_->red, fused_ ? B_->socp : nullptr,
                 fused_ ? (int)socp_blocks(g_) : 0, s, lc);
 }
@@ -478,6 +488,7 @@ int MixedBatch::read_state(int b, double* q, double* al, double* beta, cudaStrea
 int MixedBatch::write_state(int b, const double* q, const double* al, const double* beta, double sigma,
                             double tau, cudaStream_t s, std::string* err) {
   cudaError_t e = zero_slot(b, s);
+  r_valid_ = false;
   // both sets were zeroed; write into the current one, the multipliers divided by sigma
   set_sigma(b, sigma, tau, false);
   if (e == cudaSuccess) e = upload_params(s);
@@ -515,6 +526,7 @@ int MixedBatch::poisson_op(const double* b, double* phi, cudaStream_t s, LaunchC
     tb[i] = v.x;
     tl[i] = v.y;
   }
+  r_valid_ = false;   // the solve below uses f.r as scratch
   // slot 0 alone, whatever the batch holds: its parameters are restored afterwards
   std::vector<SlotParam> saved = hp_;
   for (int k = 0; k < G_; ++k) hp_[k].active = k == 0 ? 1 : 0;
