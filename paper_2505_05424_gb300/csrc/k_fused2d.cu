@@ -594,20 +594,15 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
     const int bcur = t % 3, bprev = (t + 2) % 3;
     const float2* tcur = btiles + bcur * kBetaTile;
     const float2* tprev = btiles + bprev * kBetaTile;
+    // every thread waits for the tile of cone time t itself; a wait that gives up
+    // is made uniform at the barrier after step A
+    bool ok = true;
     if (t <= g.T - 1) {
-      const bool ok = bar_wait(&bars[bcur], phase[bcur]);
+      ok = bar_wait(&bars[bcur], phase[bcur]);
       if (ok) {
         phase[bcur] ^= 1u;
         inflight[bcur] = false;
       }
-      if (__syncthreads_or(!ok)) { failed = true; break; }
-    }
-    // prefetch the next cone time's beta into buffer (t+1) % 3 = (t-2) % 3, whose
-    // last reader (step C of t-1) every thread has left at the barrier above
-    if (tid == 0 && t + 1 <= tlast_cone) {
-      const int nb = (t + 1) % 3;
-      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1, slot);
-      inflight[nb] = true;
     }
     // ---------------- A: cones at time t ----------------
     if (t <= g.T - 1) {
@@ -652,7 +647,14 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
         else put_z0(ztn, ztp[lev], hc);
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(!ok)) { failed = true; break; }
+    // prefetch the next cone time's beta into buffer (t+1) % 3 = (t-2) % 3, whose
+    // last reader (step C of t-1) every thread has left at the barrier above
+    if (tid == 0 && t + 1 <= tlast_cone) {
+      const int nb = (t + 1) % 3;
+      issue_beta(&tmb, btiles + nb * kBetaTile, &bars[nb], y0 - 2, x0 - 1, t + 1, slot);
+      inflight[nb] = true;
+    }
     // ---------------- B: faces at time node t ----------------
     const bool write_node = t >= ta && ((t < tb) || (last_chunk && t == g.T));
     if (t >= ta) {

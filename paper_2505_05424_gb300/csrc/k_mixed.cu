@@ -440,74 +440,56 @@ __device__ __forceinline__ void block_reduce_store(const float* accf, const doub
   }
 }
 
+// One node's share of the stopping measures: its cone (t < T), its faces along
+// every axis (the face after the node), and the node itself.
 template <int D>
-__global__ void __launch_bounds__(kThreads, D == 2 ? 3 : 2) k_kkt_cones(Geo g, MxFields fb, double* partials_all, int use_z) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const MxFields f = slot_view(fb, g, slot);
-  const float sg = fb.sp[slot].sg.x + fb.sp[slot].sg.y;
-  double* partials = partials_all + slot * kkt_partials_len_slot(g);
+__device__ __forceinline__ void kkt_cone(const Geo& g, const MxFields& f, float sg, long long i, long long p,
+                                         int use_z, float* acc) {
   constexpr int K = 4 * D + 2;
-  float acc[R_NSLOTS];
-  double accd[R_NSLOTS];
-  for (int k = 0; k < R_NSLOTS; ++k) { acc[k] = 0.f; accd[k] = 0.0; }
   const long long n0 = (long long)g.T * g.P;
   const float s_default = 0.70710678118654752f;
   const float ih0 = (float)g.invh[0];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i - (long long)plane_of(g, i) * g.P;
-    float x[K - 1];
-    gather_Fq<D>(g, f.q, i, p, x);
-    const float2 gp = grad_pair(f.phi, i, i + g.P, ih0);
-    const float aphi = gp.x + gp.y;
-    const float q0 = x[0];
-    const float dq = grad_minus(gp, q0);
-    acc[R_PRIM] += dq * dq;
-    acc[R_APHI] += aphi * aphi;
-    acc[R_Q] += q0 * q0;
-    float ss = 0.f;
+  float x[K - 1];
+  gather_Fq<D>(g, f.q, i, p, x);
+  const float2 gp = grad_pair(f.phi, i, i + g.P, ih0);
+  const float aphi = gp.x + gp.y;
+  const float q0 = x[0];
+  const float dq = grad_minus(gp, q0);
+  acc[R_PRIM] += dq * dq;
+  acc[R_APHI] += aphi * aphi;
+  acc[R_Q] += q0 * q0;
+  float ss = 0.f;
 #pragma unroll
-    for (int j = 1; j < K - 1; ++j) ss += x[j] * x[j];
-    const float om = f.omega ? f.omega[p] : 1.f;
-    const float fv = q0 + 0.125f * om * ss;
-    const float a0 = sg * (f.al[0][i].x + f.al[0][i].y);
-    const float m = fv + a0;
-    const float rc = a0 - (m > 0.f ? m : 0.f);
-    acc[R_COMP0] += rc * rc;
-    acc[R_ALPHA0] += a0 * a0;
-    acc[R_F] += fv * fv;
-    const float s = f.somega ? f.somega[p] : s_default;
-    if (use_z) {
-      float r = (f.z[i] - 1.f) + q0;
-      acc[R_SOCP] += r * r;
+  for (int j = 1; j < K - 1; ++j) ss += x[j] * x[j];
+  const float om = f.omega ? f.omega[p] : 1.f;
+  const float fv = q0 + 0.125f * om * ss;
+  const float a0 = sg * (f.al[0][i].x + f.al[0][i].y);
+  const float m = fv + a0;
+  const float rc = a0 - (m > 0.f ? m : 0.f);
+  acc[R_COMP0] += rc * rc;
+  acc[R_ALPHA0] += a0 * a0;
+  acc[R_F] += fv * fv;
+  const float s = f.somega ? f.somega[p] : s_default;
+  if (use_z) {
+    float r = (f.z[i] - 1.f) + q0;
+    acc[R_SOCP] += r * r;
 #pragma unroll
-      for (int j = 1; j < K - 1; ++j) {
-        r = fmaf(-s, x[j], f.z[(long long)j * n0 + i]);
-        acc[R_SOCP] += r * r;
-      }
-      r = (f.z[(long long)(K - 1) * n0 + i] - 1.f) - q0;
+    for (int j = 1; j < K - 1; ++j) {
+      r = fmaf(-s, x[j], f.z[(long long)j * n0 + i]);
       acc[R_SOCP] += r * r;
     }
-    const float2 bK = f.beta[(long long)(K - 1) * n0 + i], b0 = f.beta[i];
-    const float fbb = sg * ((bK.x - b0.x) + (bK.y - b0.y));
-    acc[R_SOCD] += (fbb + a0) * (fbb + a0);
-    acc[R_FBB] += fbb * fbb;
+    r = (f.z[(long long)(K - 1) * n0 + i] - 1.f) - q0;
+    acc[R_SOCP] += r * r;
   }
-  block_reduce_store(acc, accd, partials + (long long)blockIdx.x * R_NSLOTS);
+  const float2 bK = f.beta[(long long)(K - 1) * n0 + i], b0 = f.beta[i];
+  const float fbb = sg * ((bK.x - b0.x) + (bK.y - b0.y));
+  acc[R_SOCD] += (fbb + a0) * (fbb + a0);
+  acc[R_FBB] += fbb * fbb;
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, 3) k_kkt_faces(Geo g, MxFields fb, int d, double* partials_all) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const MxFields f = slot_view(fb, g, slot);
-  const float sg = fb.sp[slot].sg.x + fb.sp[slot].sg.y;
-  double* partials = partials_all + slot * kkt_partials_len_slot(g) + (long long)(1 + d) * kKktBlocks * R_NSLOTS;
-  float acc[R_NSLOTS];
-  double accd[R_NSLOTS];
-  for (int k = 0; k < R_NSLOTS; ++k) { acc[k] = 0.f; accd[k] = 0.0; }
-  const long long n = (long long)(g.T + 1) * g.P;
+__device__ __forceinline__ void kkt_face(const Geo& g, const MxFields& f, float sg, int d, long long i, int t,
+                                         long long p, float* acc, float2* dual) {
   const long long n0 = (long long)g.T * g.P;
   const float s_default = 0.70710678118654752f;
   const long long s = g.sst[d];
@@ -516,92 +498,100 @@ __global__ void __launch_bounds__(kThreads, 3) k_kkt_faces(Geo g, MxFields fb, i
   const float2* a0 = f.al[0];
   const int cbase = 1 + 4 * d;
   const float ih = (float)g.invh[1 + d];
-  float2 dual = make_float2(0.f, 0.f);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int t = plane_of(g, i);
-    const long long p = i - (long long)t * g.P;
-    const int j = coord(g, p, d);
-    if (j > g.N[d] - 2) continue;
-    const float2 gp = grad_pair(f.phi, i, i + s, ih);
-    const float aphi = gp.x + gp.y;
-    const float q = qd[i];
-    const float dq = grad_minus(gp, q);
-    acc[R_PRIM] += dq * dq;
-    acc[R_APHI] += aphi * aphi;
-    acc[R_Q] += q * q;
-    float den = 0.f, fbb = 0.f;
-    const float om_l = f.omega ? f.omega[p] : 1.f, om_r = f.omega ? f.omega[p + s] : 1.f;
-    const float s_l = f.somega ? f.somega[p] : s_default, s_r = f.somega ? f.somega[p + s] : s_default;
-    if (t <= g.T - 1) {
-      den += om_r * a0[i + s].x + om_l * a0[i].x;
-      fbb += s_r * f.beta[(long long)(cbase + 0) * n0 + i + s].x + s_l * f.beta[(long long)(cbase + 1) * n0 + i].x;
-    }
-    if (t >= 1) {
-      den += om_r * a0[i - g.P + s].x + om_l * a0[i - g.P].x;
-      fbb += s_r * f.beta[(long long)(cbase + 2) * n0 + i - g.P + s].x +
-             s_l * f.beta[(long long)(cbase + 3) * n0 + i - g.P].x;
-    }
-    den *= 0.25f * sg;
-    fbb *= sg;
-    const float gv = den * q;
-    const float a = sg * (ad[i].x + ad[i].y);
-    acc[R_COMPD] += (a - gv) * (a - gv);
-    acc[R_ALPHAB] += a * a;
-    acc[R_G] += gv * gv;
-    // dual objective term: each ratio rounded once in FP32, the sum carried as a
-    // two-float (no FP64 division on the per-element path)
-    if (den > 0.f) dual = ff_add_f(dual, -(0.5f * a) * (a / den));
-    acc[R_SOCD] += (fbb + a) * (fbb + a);
-    acc[R_FBB] += fbb * fbb;
+  const float2 gp = grad_pair(f.phi, i, i + s, ih);
+  const float aphi = gp.x + gp.y;
+  const float q = qd[i];
+  const float dq = grad_minus(gp, q);
+  acc[R_PRIM] += dq * dq;
+  acc[R_APHI] += aphi * aphi;
+  acc[R_Q] += q * q;
+  float den = 0.f, fbb = 0.f;
+  const float om_l = f.omega ? f.omega[p] : 1.f, om_r = f.omega ? f.omega[p + s] : 1.f;
+  const float s_l = f.somega ? f.somega[p] : s_default, s_r = f.somega ? f.somega[p + s] : s_default;
+  if (t <= g.T - 1) {
+    den += om_r * a0[i + s].x + om_l * a0[i].x;
+    fbb += s_r * f.beta[(long long)(cbase + 0) * n0 + i + s].x + s_l * f.beta[(long long)(cbase + 1) * n0 + i].x;
   }
-  accd[R_DUALOBJ] = ff_to_double(dual);
-  block_reduce_store(acc, accd, partials + (long long)blockIdx.x * R_NSLOTS);
+  if (t >= 1) {
+    den += om_r * a0[i - g.P + s].x + om_l * a0[i - g.P].x;
+    fbb += s_r * f.beta[(long long)(cbase + 2) * n0 + i - g.P + s].x +
+           s_l * f.beta[(long long)(cbase + 3) * n0 + i - g.P].x;
+  }
+  den *= 0.25f * sg;
+  fbb *= sg;
+  const float gv = den * q;
+  const float a = sg * (ad[i].x + ad[i].y);
+  acc[R_COMPD] += (a - gv) * (a - gv);
+  acc[R_ALPHAB] += a * a;
+  acc[R_G] += gv * gv;
+  // dual objective term: each ratio rounded once in FP32, the sum carried as a
+  // two-float (no FP64 division on the per-element path)
+  if (den > 0.f) *dual = ff_add_f(*dual, -(0.5f * a) * (a / den));
+  acc[R_SOCD] += (fbb + a) * (fbb + a);
+  acc[R_FBB] += fbb * fbb;
 }
 
-// Nodes: A^*alpha + c (in two-float arithmetic: the divergence of alpha cancels
+// A^*alpha + c at a node (in two-float arithmetic: the divergence of alpha cancels
 // against c to the level of the dual residual) and <c, phi> in FP64.
 template <int D>
-__global__ void k_kkt_nodes(Geo g, MxFields fb, double* partials_all) {
+__device__ __forceinline__ void kkt_node(const Geo& g, const MxFields& f, float2 sg2, long long i, int t,
+                                         long long p, float* acc, double* dres, double* cphi) {
+  float2 v = make_float2(0.f, 0.f);
+  const float ih0 = (float)g.invh[0];
+  if (t >= 1) v = ff_add(v, ff_mul_f(f.al[0][i - g.P], ih0));
+  if (t < g.T) v = ff_add(v, ff_mul_f(ff_neg(f.al[0][i]), ih0));
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int x = coord(g, p, d);
+    const float2* ad = f.al[1 + d];
+    const long long s = g.sst[d];
+    const float ih = (float)g.invh[1 + d];
+    if (x >= 1) v = ff_add(v, ff_mul_f(ad[i - s], ih));
+    if (x <= g.N[d] - 2) v = ff_add(v, ff_mul_f(ff_neg(ad[i]), ih));
+  }
+  v = ff_mul(v, sg2);   // A^* alpha = sigma A^*(alpha / sigma)
+  double c = 0.0;
+  if (t == 0) c += f.m0[p];
+  if (t == g.T) c -= f.m1[p];
+  if (c != 0.0) {
+    const double res = ff_to_double(v) + c;
+    *dres += res * res;
+    *cphi += c * ff_to_double(f.phi[i]);
+  } else {
+    const float res = v.x + v.y;
+    acc[R_DUALRES] += res * res;
+  }
+}
+
+// All stopping-measure sums in one pass over the nodes (one partial row per block).
+template <int D>
+__global__ void __launch_bounds__(kThreads, D == 2 ? 2 : 1) k_kkt(Geo g, MxFields fb, double* partials_all, int use_z) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
   const float2 sg2 = fb.sp[slot].sg;
-  double* partials = partials_all + slot * kkt_partials_len_slot(g) + (long long)(1 + D) * kKktBlocks * R_NSLOTS;
+  const float sg = sg2.x + sg2.y;
+  double* partials = partials_all + slot * kkt_partials_len_slot(g);
   float acc[R_NSLOTS];
-  double accd[R_NSLOTS];
-  for (int k = 0; k < R_NSLOTS; ++k) { acc[k] = 0.f; accd[k] = 0.0; }
+  for (int k = 0; k < R_NSLOTS; ++k) acc[k] = 0.f;
+  double dres = 0.0, cphi = 0.0;
+  float2 dual = make_float2(0.f, 0.f);
   const long long n = (long long)(g.T + 1) * g.P;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int t = plane_of(g, i);
     const long long p = i - (long long)t * g.P;
-    float2 v = make_float2(0.f, 0.f);
-    const float ih0 = (float)g.invh[0];
-    if (t >= 1) v = ff_add(v, ff_mul_f(f.al[0][i - g.P], ih0));
-    if (t < g.T) v = ff_add(v, ff_mul_f(ff_neg(f.al[0][i]), ih0));
+    if (t < g.T) kkt_cone<D>(g, f, sg, i, p, use_z, acc);
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int x = coord(g, p, d);
-      const float2* ad = f.al[1 + d];
-      const long long s = g.sst[d];
-      const float ih = (float)g.invh[1 + d];
-      if (x >= 1) v = ff_add(v, ff_mul_f(ad[i - s], ih));
-      if (x <= g.N[d] - 2) v = ff_add(v, ff_mul_f(ff_neg(ad[i]), ih));
-    }
-    v = ff_mul(v, sg2);   // A^* alpha = sigma A^*(alpha / sigma)
-    double c = 0.0;
-    if (t == 0) c += f.m0[p];
-    if (t == g.T) c -= f.m1[p];
-    if (c != 0.0) {
-      const double res = ff_to_double(v) + c;
-      accd[R_DUALRES] += res * res;
-      accd[R_CPHI] += c * ff_to_double(f.phi[i]);
-    } else {
-      const float res = v.x + v.y;
-      acc[R_DUALRES] += res * res;
-    }
+    for (int d = 0; d < D; ++d)
+      if (coord(g, p, d) <= g.N[d] - 2) kkt_face<D>(g, f, sg, d, i, t, p, acc, &dual);
+    kkt_node<D>(g, f, sg2, i, t, p, acc, &dres, &cphi);
   }
+  double accd[R_NSLOTS];
+  for (int k = 0; k < R_NSLOTS; ++k) accd[k] = 0.0;
+  accd[R_DUALRES] = dres;
+  accd[R_CPHI] = cphi;
+  accd[R_DUALOBJ] = ff_to_double(dual);
   block_reduce_store(acc, accd, partials + (long long)blockIdx.x * R_NSLOTS);
 }
 
@@ -695,11 +685,9 @@ template <int D>
 void launch_kkt_tmpl(const Geo& g, int G, const MxFields& f, double* partials, double* out,
                      const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc) {
   const int kb = kkt_blocks(g);
-  k_kkt_cones<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, partials, socp_part ? 0 : 1);
-  for (int d = 0; d < D; ++d) k_kkt_faces<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, d, partials);
-  k_kkt_nodes<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, partials);
-  k_kkt_final<<<G, kThreads, 0, s>>>(g, f.sp, partials, D + 2, kb, out, socp_part, nsocp);
-  lc.launched(KID_KKT, D + 3);
+  k_kkt<D><<<dim3(kb, G), kThreads, 0, s>>>(g, f, partials, socp_part ? 0 : 1);
+  k_kkt_final<<<G, kThreads, 0, s>>>(g, f.sp, partials, 1, kb, out, socp_part, nsocp);
+  lc.launched(KID_KKT, 2);
 }
 
 }  // namespace
