@@ -382,7 +382,7 @@ __global__ void k_update_qd(Geo g, MxFields fb, int d) {
 
 // Line 6: beta += tau sigma (z - B F q - d).
 template <int D>
-__global__ void k_update_beta(Geo g, MxFields fb) {
+__global__ void __launch_bounds__(kThreads, 3) k_update_beta(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const float ts = fb.sp[slot].tau;
