@@ -442,7 +442,7 @@ constexpr int kOffZ = 3 * kBetaTileBytes;                 // ztn [4][VNH] floats
 constexpr int kOffZP = kOffZ + 4 * VNH * 4;               // ztp [2][4][VNH] floats
 constexpr int kOffQ1 = kOffZP + 2 * 4 * VNH * 4;          // [2][VNQ1] floats
 constexpr int kOffQ2 = kOffQ1 + 2 * VNQ1 * 4;             // [2][VNQ2] floats
-constexpr int kOffW1 = kOffQ2 + 2 * VNQ2 * 4;             // [VNQ1] two-float q - alpha/sigma
+constexpr int kOffW1 = kOffQ2 + 2 * VNQ2 * 4;             // [VNQ1] two-float q - alpha/sigma - A phi
 constexpr int kOffW2 = kOffW1 + VNQ1 * 8;                 // [VNQ2] two-float
 constexpr int kOffBar = (kOffW2 + VNQ2 * 8 + 15) / 16 * 16;
 constexpr int kSmemV2 = kOffBar + 64;
@@ -505,12 +505,6 @@ __device__ __forceinline__ void put_z0(float (*ztn)[VNH], float (*ztp)[VNH], int
     ztp[v][hc] = 0.f;
   }
 }
-// a - b of two two-float values, unnormalised
-__device__ __forceinline__ float2 ff_diff(float2 a, float2 b) {
-  const float2 d = two_sum(a.x, -b.x);
-  return make_float2(d.x, d.y + (a.y - b.y));
-}
-
 // z of cone (t, x, y) from the iteration-k q (global) and a beta tile, in two-float
 // arithmetic as cone_z; false for a cone outside the grid.
 __device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, const float2* tile, int t, int x,
@@ -586,7 +580,7 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
 
   float zc[K2], zp[K2];
   float q0c = 0.f, q0p = 0.f, socp = 0.f;
-  float2 w0c = make_float2(0.f, 0.f), w0p = make_float2(0.f, 0.f);   // q_0 - alpha_0/sigma, cones t, t-1
+  float2 w0c = make_float2(0.f, 0.f), w0p = make_float2(0.f, 0.f);   // q_0 - alpha_0/sigma - A_0 phi, cones t, t-1
   bool failed = false;
 
   for (int t = tstart; t <= tb; ++t) {
@@ -626,7 +620,7 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
               a.aln[0][i] = aln;
             }
             q0c = qn;
-            w0c = ff_add_f(ff_neg(aln), qn);
+            w0c = ff_add(ff_add_f(ff_neg(aln), qn), ff_neg(gp));   // q - alpha/sigma - A phi
           }
 #pragma unroll
           for (int j = 0; j < K2; ++j) zc[j] = ff_round(z[j]);
@@ -690,7 +684,7 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
               a.qn[1][i] = qv;
               a.aln[1][i] = aln;
             }
-            wv = ff_add_f(ff_neg(aln), qv);
+            wv = ff_add(ff_add_f(ff_neg(aln), qv), ff_neg(gp));   // q - alpha/sigma - A phi
           }
           sq1[lev][e] = qv;
           sw1[e] = wv;
@@ -725,7 +719,7 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
               a.qn[2][i] = qv;
               a.aln[2][i] = aln;
             }
-            wv = ff_add_f(ff_neg(aln), qv);
+            wv = ff_add(ff_add_f(ff_neg(aln), qv), ff_neg(gp));   // q - alpha/sigma - A phi
           }
           sq2[lev][f] = qv;
           sw2[f] = wv;
@@ -762,43 +756,21 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
       socp = fmaf(inc, inc, socp);
       a.betan[(K2 - 1) * n0 + i] = ff_add_f(bt(tprev, K2 - 1, xh, yh), ts * inc);
     }
-    // the next iteration's residual at the owned node of time t
+    // the next iteration's residual at the owned node of time t:
+    // r = A^*(q - alpha/sigma) - c/sigma - A^*A phi = A^*(q - alpha/sigma - A phi) - c/sigma,
+    // with q - alpha/sigma - A phi of the node's faces from steps A and B
     if (a.r && own_ok && write_node) {
       const int i = t * P + xo * N1 + yo;
       const int p = xo * N1 + yo;
-      float2 acc = make_float2(0.f, 0.f), lap = make_float2(0.f, 0.f);
-      const float2 xi = a.phi[i];
-      {
-        float2 sd = make_float2(0.f, 0.f);
-        if (t >= 1) {
-          acc = ff_add(acc, ff_mul_f(w0p, ih0));
-          sd = ff_add(sd, ff_diff(xi, a.phi[i - P]));
-        }
-        if (t < g.T) {
-          acc = ff_add(acc, ff_neg(ff_mul_f(w0c, ih0)));
-          sd = ff_add(sd, ff_diff(xi, a.phi[i + P]));
-        }
-        lap = ff_add(lap, ff_mul_f(sd, ih0 * ih0));
-      }
-      {
-        // x-faces j = xo - 1 (row lx) and j = xo (row lx + 1); zero beyond the walls
-        acc = ff_add(acc, ff_mul_f(ff_add(sw1[lx * VY + ly], ff_neg(sw1[(lx + 1) * VY + ly])), ih1));
-        float2 sd = make_float2(0.f, 0.f);
-        if (xo >= 1) sd = ff_add(sd, ff_diff(xi, a.phi[i - N1]));
-        if (xo <= g.N[0] - 2) sd = ff_add(sd, ff_diff(xi, a.phi[i + N1]));
-        lap = ff_add(lap, ff_mul_f(sd, ih1 * ih1));
-      }
-      {
-        acc = ff_add(acc, ff_mul_f(ff_add(sw2[lx * (VY + 1) + ly], ff_neg(sw2[lx * (VY + 1) + ly + 1])), ih2));
-        float2 sd = make_float2(0.f, 0.f);
-        if (yo >= 1) sd = ff_add(sd, ff_diff(xi, a.phi[i - 1]));
-        if (yo <= g.N[1] - 2) sd = ff_add(sd, ff_diff(xi, a.phi[i + 1]));
-        lap = ff_add(lap, ff_mul_f(sd, ih2 * ih2));
-      }
+      float2 acc = make_float2(0.f, 0.f);
+      if (t >= 1) acc = ff_add(acc, ff_mul_f(w0p, ih0));
+      if (t < g.T) acc = ff_add(acc, ff_neg(ff_mul_f(w0c, ih0)));
+      // faces j = x - 1 / x (and y - 1 / y); the slots beyond the walls hold zero
+      acc = ff_add(acc, ff_mul_f(ff_add(sw1[lx * VY + ly], ff_neg(sw1[(lx + 1) * VY + ly])), ih1));
+      acc = ff_add(acc, ff_mul_f(ff_add(sw2[lx * (VY + 1) + ly], ff_neg(sw2[lx * (VY + 1) + ly + 1])), ih2));
       if (t == 0) acc = ff_add(acc, ff_neg(ff_mul(a.c0[p], a.isg)));
       if (t == g.T) acc = ff_add(acc, ff_mul(a.c1[p], a.isg));
-      const float2 rr = ff_add(acc, ff_neg(lap));
-      a.r[i] = rr.x + rr.y;
+      a.r[i] = acc.x + acc.y;
     }
     q0p = q0c;
     w0p = w0c;
