@@ -452,6 +452,8 @@ constexpr unsigned kSpinV2 = 1u << 25;
 // ring cones), so phase A takes one round; 552 faces take two
 constexpr int kThreadsV2 = 352;
 constexpr int kMinBlocksV2 = FUSED_V2_MIN_BLOCKS;
+// cone times per CTA: each chunk recomputes one cone time before it (1/kTchunkV2 extra)
+constexpr int kTchunkV2 = 16;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -812,7 +814,7 @@ namespace dot {
 bool fused2d_tma_supported(const Geo& g) { return g.D == 2 && g.N[1] % 2 == 0; }
 
 long long fused2d_tma_blocks(const Geo& g) {
-  const int tchunk = g.T <= 16 ? g.T : 16;
+  const int tchunk = g.T <= kTchunkV2 ? g.T : kTchunkV2;
   return (long long)((g.N[0] + VX - 1) / VX) * ((g.N[1] + VY - 1) / VY) * ((g.T + tchunk - 1) / tchunk);
 }
 
@@ -830,7 +832,7 @@ bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& 
   a.phi = f.phi;
   a.somega = f.somega;
   a.ts = 0.f;
-  a.tchunk = g.T <= 16 ? g.T : 16;
+  a.tchunk = g.T <= kTchunkV2 ? g.T : kTchunkV2;
   a.nchunk = (g.T + a.tchunk - 1) / a.tchunk;
   a.sp = f.sp;
   a.socp_part = socp_part;

@@ -565,7 +565,7 @@ __device__ __forceinline__ void kkt_node(const Geo& g, const MxFields& f, float2
 
 // All stopping-measure sums in one pass over the nodes (one partial row per block).
 template <int D>
-__global__ void __launch_bounds__(kThreads, D == 2 ? 2 : 1) k_kkt(Geo g, MxFields fb, double* partials_all, int use_z) {
+__global__ void __launch_bounds__(kThreads, 1) k_kkt(Geo g, MxFields fb, double* partials_all, int use_z) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
