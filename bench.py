@@ -185,7 +185,7 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
 
 # DRAM bytes (read + write) of one launch, from an ncu capture of the mix256 workload
 # (profiles/k_fused2d_tma_mix256.md); valid while the kernel is unchanged since.
-NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"): 596.381440e6 + 474.390784e6}
+NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"): 597.195264e6 + 475.236096e6}
 
 
 # ---- replicas: one process per GPU, independent solves, no data-path collective --
