@@ -5,7 +5,8 @@ each output is the end of at most ~20 roundings with an amplification of at most
 ~10 (the divisions in the cone projection and the diagonal solve), so a step
 agrees to 2e-5 relative to the field's maximum.  The refined Poisson solve
 (FP32 solve, exact two-float residual, FP32 correction) is accurate to u^2 times
-the conditioning of the DCT pair, tested at 1e-9.  Whole solves: KKT <= 1e-6 and
+the conditioning of the DCT pair and of the Laplacian, tested at 1e-9 up to 96
+points per axis and scaled with the Laplacian's condition number beyond.  Whole solves: KKT <= 1e-6 and
 the objective against the FP64 oracle's continued to eta <= 1e-7.
 """
 import numpy as np
@@ -46,7 +47,14 @@ def centred(v):
     return v - v.mean()
 
 
-@pytest.mark.parametrize("D,T,N", GRIDS)
+# grids whose tcgen05 passes have more work units (128-row tile x column tile) than
+# the GPU has SMs, so that each persistent CTA runs several units through its
+# stage ring and both TMEM accumulators: 256^2 x 64 (2-4 units per CTA) and
+# 512^2 x 8 (a 9-long time axis: about 14 units per CTA)
+MANY_UNITS = [(2, 64, [256, 256]), (2, 8, [512, 512])]
+
+
+@pytest.mark.parametrize("D,T,N", GRIDS + MANY_UNITS)
 def test_refined_poisson(D, T, N):
     rng = np.random.default_rng(500 + T)
     g = O.Grid(D, T, N)
@@ -55,11 +63,22 @@ def test_refined_poisson(D, T, N):
     _, _, gpu = pair(D, T, N, r0, r0, prec="mixed")
     phi = gpu.dot_poisson(b)
     ref = O.poisson(g, b)
-    assert rel_err(centred(phi), ref) < 1e-9
+    assert rel_err(centred(phi), ref) < refined_tol(T, N)
     gpu.close()
 
 
-@pytest.mark.parametrize("D,T,N", [(2, 5, [32, 36]), (2, 64, [128, 128]), (3, 3, [8, 12, 16]), (2, 3, [8, 300])])
+def refined_tol(T, N):
+    """Bound on the refined solve's error relative to max|phi|.  The FP32 solve's
+    error scales with the condition number of the Neumann Laplacian on the longest
+    axis, (2 n / pi)^2 for n points, and the refinement leaves a multiple of it: 1e-9
+    up to 96 points, growing as n^2 beyond (measured 5.0e-10 at 128^2 x 64, 1.05e-9
+    at 192^2 x 32, 3.3e-9 at 256^2 x 64, 7.6e-9 at 512^2 x 8)."""
+    n = max([T + 1] + list(N))
+    return 1e-9 * max(1.0, (n / 96.0) ** 2)
+
+
+@pytest.mark.parametrize("D,T,N", [(2, 5, [32, 36]), (2, 64, [128, 128]), (3, 3, [8, 12, 16]), (2, 3, [8, 300])]
+                         + MANY_UNITS)
 def test_poisson_runs_entirely_on_tensor_cores(D, T, N):
     """Every axis fits a tcgen05 tile: each of the two solves of a refined Poisson
     solve is D spatial passes each way plus two time passes, none on the SIMT
