@@ -299,6 +299,14 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
     if (ok) {
       const int wq = warp & 3;                 // TMEM lane quarter this warp may access
       const int row = wq * 32 + lane;          // row within the tile
+      // KEEP: this warp's copy of the time eigenvalues lam_0(n0 .. n0 + nout) in
+      // stage 0's X tile, which no TMA load or MMA touches once the accumulator is
+      // complete (one copy per warp: no barrier across warps)
+      float* slam = reinterpret_cast<float*>(sx[0]) + (warp - 2) * kMaxN;
+      if (pa.mode == TC_KEEP) {
+        for (int i = lane; i < nout; i += 32) slam[i] = n0 + i < pa.K ? pa.lam[0][n0 + i] : 1.f;
+        __syncwarp();
+      }
       long long out_base = 0, col_stride = 1;
       bool valid;
       float lsp = 0.f;        // KEEP: spatial part of the eigenvalue
@@ -346,8 +354,9 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int k = n0 + c0 + j;
-            const float lam = (k < pa.K ? pa.lam[0][k] : 1.f) + lsp;
-            w[j] = (k == 0 && zero_mode) ? 0.f : __uint_as_float(v[j]) / lam;
+            const float lam = slam[c0 + j] + lsp;
+            // fast division (within 2 ulp for the eigenvalue range, 0 < lam < 2^126)
+            w[j] = (k == 0 && zero_mode) ? 0.f : __fdividef(__uint_as_float(v[j]), lam);
           }
           float* o = pa.out + out_base + n0 + c0;
           if (n0 + c0 + 16 <= pa.K) {
