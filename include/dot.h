@@ -70,6 +70,11 @@ typedef struct {
                               check_every iterations; 0 = never; default 10 */
   double obstacle_weight;  /* omega on masked cells (Sec. 5.4); default 1e-6 */
   double max_seconds;      /* wall-clock limit per dot_solve call; 0 = none */
+  int use_graphs;          /* mixed path: replay each check period of dot_solve (the
+                              check_every iterations and the stopping measures) from
+                              a CUDA graph captured on first use; 0 = launch kernel by
+                              kernel, as solves under dot_profile always do.  The
+                              results are the same bit for bit; default 1 */
 } dot_options;
 
 /* Index of each value in the kkt[] array filled by dot_get / dot_kkt. */

@@ -170,6 +170,10 @@ struct dot_ctx {
   size_t ev_n = 0;
   double prof_ms[KID_COUNT] = {0};
   long prof_cnt[KID_COUNT] = {0};
+  // CUDA-graph replay of check periods (dot_solve): the private stream the period
+  // is captured on (the caller's stream may be the legacy default stream, which
+  // cannot be captured)
+  cudaStream_t cap = nullptr;
 };
 
 void dot::problem_of(const dot_ctx* c, dot_grid* g, dot_options* opt, void** stream, std::vector<double>* rho0,
@@ -219,6 +223,8 @@ void prof_flush(dot_ctx* c) {
     if (cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) {
       c->prof_ms[kid] += ms;
       c->prof_cnt[kid] += 1;
+    } else {
+      cudaGetLastError();   // a timing query never fails the solve
     }
   }
   c->ev_n = 0;
@@ -273,6 +279,87 @@ int compute_kkt(dot_ctx* c) {
   return DOT_OK;
 }
 
+constexpr int kNoGraph = 1000;   // PeriodGraphs::period: no graph, run the period directly
+
+// Check periods of dot_solve replayed from CUDA graphs: one graph per parity of
+// the iterate buffers, captured on first use from the path's own launch sequence
+// (ce iterations, the stopping-measure kernels, the copies of their sums and of
+// the pipeline error flag into pinned host memory) and destroyed when the solve
+// returns.  Between periods the penalty is applied outside the graph: the kernels
+// read sigma and tau from device memory.  Profiled solves (dot_profile) launch
+// kernel by kernel: an event node at every kernel boundary inside the graph costs
+// more than the graph saves (1,470 against 1,500 iterations/s on 256^2 x 64).
+class PeriodGraphs {
+ public:
+  explicit PeriodGraphs(dot_ctx* c) : c_(c) {}
+  ~PeriodGraphs() {
+    if (exec_[0] || exec_[1]) cudaStreamSynchronize(c_->stream);
+    for (auto& e : exec_)
+      if (e) cudaGraphExecDestroy(e);
+  }
+  // One period: DOT_OK with the stopping measures in c->kkt, an error code, or
+  // kNoGraph when this period cannot come from a graph (the caller then runs it
+  // kernel by kernel).
+  int period(int ce) {
+    dot_ctx* c = c_;
+    if (broken_ || c->prof || !c->opt.use_graphs || !c->path->graphable() || c->path->residual_carried())
+      return kNoGraph;
+    c->path->set_penalty(c->sigma, c->opt.tau, c->stream, counter(c));
+    const int par = c->path->parity() & 1;
+    if (!exec_[par] && !capture(par, ce)) {
+      broken_ = true;
+      return kNoGraph;
+    }
+    int* hflag = reinterpret_cast<int*>(c->h_red + R_NSLOTS);
+    *hflag = 0;
+    DOT_CK(c, cudaGraphLaunch(exec_[par], c->stream));
+    c->path->set_parity(par ^ (ce & 1));
+    c->launches += launches_[par];
+    c->iters += ce;
+    DOT_CK(c, cudaStreamSynchronize(c->stream));
+    if (*hflag) return fail(c, DOT_ECUDA, "a tensor-core pipeline wait timed out (kernel returned early)");
+    finish_kkt(c, c->h_red);
+    return DOT_OK;
+  }
+
+ private:
+  bool capture(int par, int ce) {
+    dot_ctx* c = c_;
+    if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      c->cap = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    long n = 0;
+    LaunchCounter lc{&n};
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      for (int it = 0; it < ce; ++it) c->path->iterate(c->sigma, c->opt.tau, c->cap, lc);
+      c->path->kkt(c->cap, lc);
+      cudaMemcpyAsync(c->h_red, c->path->red_out(), sizeof(double) * R_NSLOTS, cudaMemcpyDeviceToHost, c->cap);
+      if (c->path->error_flag())
+        cudaMemcpyAsync(c->h_red + R_NSLOTS, c->path->error_flag(), sizeof(int), cudaMemcpyDeviceToHost, c->cap);
+      e = cudaStreamEndCapture(c->cap, &graph);
+    }
+    c->path->set_parity(par);   // the capture ran nothing: the buffers are where they were
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_[par], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      exec_[par] = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    launches_[par] = n;
+    return true;
+  }
+
+  dot_ctx* c_;
+  cudaGraphExec_t exec_[2] = {nullptr, nullptr};
+  long launches_[2] = {0, 0};
+  bool broken_ = false;
+};
+
 }  // namespace
 
 extern "C" {
@@ -287,6 +374,7 @@ void dot_default_options(dot_options* o) {
   o->check_every = 10;
   o->obstacle_weight = 1e-6;
   o->max_seconds = 0.0;
+  o->use_graphs = 1;
 }
 
 const char* dot_version(void) { return "dot-gb300 0.1 (sm_103a)"; }
@@ -367,19 +455,38 @@ int dot_solve(dot_ctx* c, double tol, long maxit) {
   const auto t0 = std::chrono::steady_clock::now();
   const int ce = c->opt.check_every;
   LaunchCounter lc = counter(c);
-  for (long k = 1; k <= maxit; ++k) {
-    if (c->prof) {
-      if (c->ev_n > 4096) {
-        DOT_CK(c, cudaStreamSynchronize(c->stream));
-        prof_flush(c);
+  PeriodGraphs graphs(c);
+  long k = 0;   // iterations done by this call
+  while (k < maxit) {
+    bool checked = false;
+    // a whole check period from a CUDA graph: ce iterations and the stopping
+    // measures, the same kernels in the same order as the loop below
+    if (ce > 0 && k % ce == 0 && k + ce <= maxit) {
+      const int rc = graphs.period(ce);
+      if (rc != kNoGraph) {
+        if (rc != DOT_OK) return rc;
+        k += ce;
+        checked = true;
       }
-      prof_record(c, -1);
     }
-    c->path->iterate(c->sigma, c->opt.tau, c->stream, lc);
-    ++c->iters;
-    if (ce > 0 && k % ce == 0) {
-      int rc = compute_kkt(c);
-      if (rc != DOT_OK) return rc;
+    if (!checked) {
+      if (c->prof) {
+        if (c->ev_n > 4096) {
+          DOT_CK(c, cudaStreamSynchronize(c->stream));
+          prof_flush(c);
+        }
+        prof_record(c, -1);
+      }
+      c->path->iterate(c->sigma, c->opt.tau, c->stream, lc);
+      ++c->iters;
+      ++k;
+      if (ce > 0 && k % ce == 0) {
+        const int rc = compute_kkt(c);
+        if (rc != DOT_OK) return rc;
+        checked = true;
+      }
+    }
+    if (checked) {
       const double eta = c->kkt[DOT_KKT_ETA];
       if (!std::isfinite(eta)) return fail(c, DOT_EDIVERGED, "stopping measure is not finite");
       if (tol > 0.0 && eta <= tol) return DOT_OK;
@@ -494,6 +601,7 @@ void dot_destroy(dot_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->cap) cudaStreamDestroy(c->cap);
   c->path.reset();
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->own_ws && c->ws) cudaFree(c->ws);

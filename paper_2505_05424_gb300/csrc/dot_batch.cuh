@@ -59,6 +59,8 @@ class MixedBatch {
   // iterate() flips it without running anything; set_parity puts it back.
   int parity() const { return cur_; }
   void set_parity(int p) { cur_ = p & 1; }
+  // Whether the next iterate() reuses the residual the previous one left in f.r.
+  bool residual_valid() const { return r_valid_; }
   const Geo& geo() const { return g_; }
 
   int read_fields(int b, double* rho, double* m, double* phi, cudaStream_t s, std::string* err);

@@ -64,6 +64,19 @@ class Path {
   virtual const int* error_flag() const { return nullptr; }
   // Mixed path: whether eligible DCT passes run on the tensor cores.
   virtual void set_tensor_cores(bool) {}
+
+  // Replay of whole check periods from a CUDA graph (the mixed path, whose kernels
+  // read the penalty and step from device memory).  set_penalty applies sigma and
+  // tau for the next iterations (and rescales the stored multipliers when sigma
+  // changed) outside the graph; parity says which of the two iterate buffers is
+  // current (a capture flips it without running anything); residual_carried says
+  // that the next iteration reuses a residual left by the previous one, which a
+  // period captured right after a stopping-measure check does not expect.
+  virtual bool graphable() const { return false; }
+  virtual void set_penalty(double, double, cudaStream_t, LaunchCounter) {}
+  virtual int parity() const { return 0; }
+  virtual void set_parity(int) {}
+  virtual bool residual_carried() const { return false; }
 };
 
 size_t path_workspace_bytes(const Geo& g, dot_precision prec);

@@ -568,6 +568,10 @@ class PathMixed : public Path {
   }
 
   void iterate(double sigma, double tau, cudaStream_t s, LaunchCounter lc) override {
+    set_penalty(sigma, tau, s, lc);
+    batch_.iterate(s, lc);
+  }
+  void set_penalty(double sigma, double tau, cudaStream_t s, LaunchCounter lc) override {
     if (sigma != sigma_ || tau != tau_) {
       sigma_ = sigma;
       tau_ = tau;
@@ -579,8 +583,11 @@ class PathMixed : public Path {
         batch_.upload_params(s);
       }
     }
-    batch_.iterate(s, lc);
   }
+  bool graphable() const override { return true; }
+  int parity() const override { return batch_.parity(); }
+  void set_parity(int p) override { batch_.set_parity(p); }
+  bool residual_carried() const override { return batch_.residual_valid(); }
   void kkt(cudaStream_t s, LaunchCounter lc) override { batch_.kkt(s, lc); }
   const double* red_out() const override { return batch_.red_out(); }
   const int* error_flag() const override { return batch_.error_flag(); }
