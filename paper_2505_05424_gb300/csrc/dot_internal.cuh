@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace dot {
 
 constexpr int kMaxD = 3;
@@ -48,6 +50,18 @@ inline FastDiv make_fastdiv(unsigned d) {
 
 __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
   return f.d <= 1 ? n : (__umulhi(n, f.m) >> f.sh);
+}
+
+// Opt a kernel into `bytes` of dynamic shared memory on the current device.  The
+// attribute belongs to the device, so each call site keeps a bit per device
+// (devices 0-63; others set it at every call) in `done`.
+inline void smem_optin(const void* kernel, int bytes, std::atomic<unsigned long long>* done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done->load(std::memory_order_acquire) & bit)) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && bit)
+    done->fetch_or(bit, std::memory_order_acq_rel);
 }
 
 // Grid geometry passed by value to every kernel.  Element indices of one field

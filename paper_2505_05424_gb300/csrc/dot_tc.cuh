@@ -12,7 +12,6 @@ namespace dot {
 // tiles.  Rows of X and of the tables are stored with strides that are multiples
 // of 4 floats (16-byte TMA row strides).
 bool tc_pass_supported(int K);
-int tc_smem_bytes();
 
 enum TcMode { TC_ROWS_FLAT = 0, TC_ROWS_A = 1, TC_KEEP = 2 };
 

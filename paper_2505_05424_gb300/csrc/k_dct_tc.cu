@@ -434,14 +434,10 @@ bool encode_tensor_map(CUtensorMap* m, CUtensorMapDataType type, int rank, const
 
 bool tc_pass_supported(int K) { return K >= 1 && K <= 16 * kMaxN; }
 
-int tc_smem_bytes() { return kSmemBytes; }
 
 bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_dct_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> smem_done{0};
+  smem_optin((const void*)k_dct_pass_tc, kSmemBytes, &smem_done);
   const int K = p.K;
   if (!tc_pass_supported(K) || p.ldx < K || p.ldx % 4 != 0 || p.ldb < K || p.ldb % 4 != 0) return false;
   if (((uintptr_t)p.X & 15) || ((uintptr_t)p.Bhi & 15) || ((uintptr_t)p.Blo & 15)) return false;

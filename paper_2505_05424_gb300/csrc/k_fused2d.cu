@@ -403,11 +403,8 @@ void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, 
   a.r = nullptr;
   a.c0 = a.c1 = nullptr;
   dim3 grid((unsigned)((g.N[0] + TX - 1) / TX), (unsigned)((g.N[1] + TY - 1) / TY), (unsigned)(a.nchunk * G));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fused2d, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemFused);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> smem_done{0};
+  smem_optin((const void*)k_fused2d, kSmemFused, &smem_done);
   k_fused2d<<<grid, kThreads, kSmemFused, s>>>(g, a);
   lc.launched(KID_FUSED);
 }
@@ -850,11 +847,8 @@ bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& 
                              (cuuint64_t)K2 * g.T * g.P * 8};
   const cuuint32_t box[5] = {VBW, VHX, 1, K2, 1};
   if (!encode_tensor_map(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, f.beta, dims, str, box)) return false;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fused2d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemV2);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> smem_done{0};
+  smem_optin((const void*)k_fused2d_tma, kSmemV2, &smem_done);
   dim3 grid((unsigned)((g.N[0] + VX - 1) / VX), (unsigned)((g.N[1] + VY - 1) / VY), (unsigned)(a.nchunk * G));
   k_fused2d_tma<<<grid, kThreadsV2, kSmemV2, s>>>(tm, g, a);
   lc.launched(KID_FUSED);

@@ -242,11 +242,8 @@ size_t tsolve_smem_bytes(const Geo& g) {
 template <int R>
 void launch_tsolve_r(const Geo& g, const MxPoisson& ps, const float* X, float* Y, cudaStream_t s) {
   const size_t sm = tsolve_smem_bytes(g);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_tsolve_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> smem_done{0};
+  smem_optin((const void*)k_tsolve_f32<R>, 220 * 1024, &smem_done);
   k_tsolve_f32<R><<<(unsigned)((g.P + 63) / 64), 256, sm, s>>>(g, ps.C[0], ps.lam[0], ps, X, Y);
 }
 
