@@ -40,7 +40,8 @@ WORKLOAD_DESCS = {
     "gauss32": "2D DOT 32x32 cells x 16 time steps, Gaussians sigma 0.1 at (0.3,0.3), (0.7,0.7) + floor 1e-3",
     "mix1024": ("2D DOT 1024x1024 cells x 32 time steps (the scalability case), seeded mixtures as mix256"),
 }
-WORKLOAD_SEEDS = {"mix256": 1002, "obst128": 1003, "mix3d64": 1004, "gauss32": None, "mix1024": 1005}
+WORKLOAD_SEEDS = {"mix256": 1002, "obst128": 1003, "mix3d64": 1004, "gauss32": None, "mix1024": 1005,
+                  "ex1": None, "ex2": None, "ex3": None, "ex4": None}
 # Iterations the FP64 recurrence (GPU FP64 path == oracle, lock-step tested) needs to reach
 # eta_dot <= 1e-6 on the seed-1002 instance of this workload; converts the oracle's
 # seconds per iteration into solves/s in the reference arm.  Measured by this script's
@@ -61,7 +62,8 @@ def parse():
     ap.add_argument("--fp64-maxit", type=int, default=40000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64", "mix1024"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64", "mix1024",
+                                                                "ex1", "ex2", "ex3", "ex4"])
     ap.add_argument("--serve", type=int, default=0,
                     help="serve the first SERVE requests of the seeded serving stream (2D grids "
                          "{32^2x16, 64^2x32, 128^2x32, 256^2x64}, Poisson arrivals, 20%% masked) through "

@@ -14,6 +14,9 @@ Recipes (densities are sampled at cell centres (i + 1/2)/N of [0, 1]^D):
   rect_mask       union of 3..6 axis-aligned rectangles covering 8-12% of cells
   product_pair    separable (f(x) + eps)(f(y) + eps) densities whose W2^2 is the
                   sum of the 1D values (closed-form check)
+  paper_example   the analytic 2D examples Ex-1 .. Ex-4 of Sec. 5 (Gaussians at
+                  0.25 / 0.75, a Laplace-type bump, a quartic), each normalised
+                  to unit mass on [0, 1]^2 and raised by the uniform floor delta
 """
 from __future__ import annotations
 
@@ -40,6 +43,7 @@ MIX256 = GridSpec(2, 64, 256)        # 2D 256^2 x 64, Gaussian mixtures with exa
 OBST128 = GridSpec(2, 32, 128)       # 2D 128^2 x 32, mixtures + rectangle obstacles
 MIX3D64 = GridSpec(3, 32, 64)        # 3D 64^3 x 32, anisotropic mixtures + floor 1e-4
 MIX1024 = GridSpec(2, 32, 1024)      # 2D 1024^2 x 32, mixtures as MIX256 (the scalability case)
+EX128 = GridSpec(2, 32, 128)         # the paper's Ex-1 .. Ex-4 grid (n_0, n_1, n_2) = (32, 128, 128)
 
 
 def cell_centres(N: int, D: int):
@@ -132,6 +136,34 @@ def product_pair(N: int, mu0=(0.35, 0.4), mu1=(0.65, 0.55), sig=(0.08, 0.1), eps
     return np.outer(f0, g0), np.outer(f1, g1), (f0, g0, f1, g1)
 
 
+def paper_example(k: int, N: int, delta: float = 0.0):
+    """(rho0, rho1) of Ex-k, k = 1..4 (Sec. 5): the functions the examples define,
+    sampled at the cell centres of an N x N grid, each scaled to unit mass on the
+    unit square (mean 1) and raised by delta."""
+    x = (np.arange(N) + 0.5) / N
+    X1, X2 = np.meshgrid(x, x, indexing="ij")
+    m1, m2 = 0.25, 0.75
+
+    def gauss(a, b, chi):
+        return np.exp((-(X1 - a) ** 2 - (X2 - b) ** 2) / (2.0 * chi ** 2))
+
+    def four(chi):
+        return gauss(m1, m1, chi) + gauss(m1, m2, chi) + gauss(m2, m1, chi) + gauss(m2, m2, chi)
+
+    if k == 1:
+        chi = np.sqrt(0.05)
+        v0, v1 = gauss(m1, m2, chi), gauss(m2, m1, chi)
+    elif k == 2:
+        v0, v1 = gauss(m1, m1, 0.1), four(0.05)
+    elif k == 3:
+        v0, v1 = np.exp(-3.0 * np.abs(X1 - m1) - 5.0 * np.abs(X2 - m1)), four(0.05)
+    elif k == 4:
+        v0, v1 = (X1 - 0.5) ** 4 + (X2 - 0.5) ** 4, four(0.05)
+    else:
+        raise ValueError("k must be 1..4")
+    return (v0 / v0.mean() + delta).ravel(), (v1 / v1.mean() + delta).ravel()
+
+
 def workload(name: str, seed: int | None = None):
     """(spec, rho0, rho1, mask) for a named workload with its default seed."""
     if name == "gauss32":
@@ -149,4 +181,7 @@ def workload(name: str, seed: int | None = None):
     if name == "mix3d64":
         r0, r1, m = mixture_pair(MIX3D64, 1004 if seed is None else seed)
         return MIX3D64, r0, r1, m
+    if name in ("ex1", "ex2", "ex3", "ex4"):
+        r0, r1 = paper_example(int(name[2]), EX128.N)
+        return EX128, r0, r1, None
     raise KeyError(name)
