@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=40000)
+    ap.add_argument("--check-every", type=int, default=10,
+                    help="stopping measures and penalty rule every this many iterations")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--fp64-maxit", type=int, default=40000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -253,14 +255,14 @@ def run_ours(args):
     # warm-up solves
     for w in range(args.warmup):
         r0, r1, m = instance(w)
-        s = make_solver(spec, r0, r1, m, args.prec)
+        s = make_solver(spec, r0, r1, m, args.prec, check_every=args.check_every)
         s.dot_solve(args.tol, args.maxit)
         s.close()
     # inputs resident in HBM before the timed region
     solvers = []
     for k in range(args.steps):
         r0, r1, m = instance(k)
-        s = make_solver(spec, r0, r1, m, args.prec)
+        s = make_solver(spec, r0, r1, m, args.prec, check_every=args.check_every)
         s.dot_profile(True)
         solvers.append(s)
     launches0 = sum(s.launch_count() for s in solvers)
@@ -344,7 +346,7 @@ def run_ours(args):
         r0, r1, m = instance(100 + k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s = make_solver(spec, r0, r1, m, args.prec)
+        s = make_solver(spec, r0, r1, m, args.prec, check_every=args.check_every)
         s.dot_solve(args.tol, args.maxit)
         rho, mm, phi, obj, kk = s.dot_get()
         torch.cuda.synchronize()
@@ -360,7 +362,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"{wl}: {WORKLOAD_DESCS[wl]}", "D": spec.D, "T": spec.T, "N": spec.N,
-                   "tol": args.tol, "prec": args.prec, "check_every": 10, "tau": 1.9,
+                   "tol": args.tol, "prec": args.prec, "check_every": args.check_every, "tau": 1.9,
                    "l2": "inputs larger than L2 (per-solve state > 129 MB)", "seeds": f"{base_seed}+step",
                    "parallelism": f"replicas{world}"},
         "iterations": iters, "eta_dot": etas, "objective": objs,
@@ -379,10 +381,10 @@ def run_ours(args):
     fp64_iters = None
     if not args.no_fp64 and args.prec == "mixed":
         r0, r1, m = instance(0)
-        s = make_solver(spec, r0, r1, m, "fp64")
+        s = make_solver(spec, r0, r1, m, "fp64", check_every=args.check_every)
         s.dot_solve(args.tol, 20)          # warm the kernels
         s.close()
-        s = make_solver(spec, r0, r1, m, "fp64")
+        s = make_solver(spec, r0, r1, m, "fp64", check_every=args.check_every)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc = s.dot_solve(args.tol, args.fp64_maxit)
