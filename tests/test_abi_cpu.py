@@ -71,8 +71,12 @@ def test_create_rejects_bad_arguments_before_any_device_call(lib):
     assert _create(lib, g, ok, nan)[0] == N.DOT_EINVAL
     assert _create(lib, g, np.zeros(16), ok)[0] == N.DOT_EINVAL
     o = N.DotOptions(); lib.dot_default_options(ctypes.byref(o))
-    assert abs(o.tau - 1.9) < 1e-15 and o.s_sigma == 1.25 and o.s_r == 2.0 and o.check_every == 10
-    assert o.use_graphs == 1
+    # the defaults are the paper's parameters (fixture with citations)
+    golden = os.path.join(os.path.dirname(__file__), "golden", "algorithm_parameters.txt")
+    rows = [l.split() for l in open(golden) if l.strip() and not l.startswith("#")]
+    for name, value in rows:
+        assert getattr(o, name) == float(value), name
+    assert o.check_every == 10 and o.use_graphs == 1
     o.tau = 2.0
     assert _create(lib, g, ok, ok, o)[0] == N.DOT_EINVAL
     o.tau = 1.9; o.s_r = 1.0
