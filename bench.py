@@ -46,7 +46,7 @@ WORKLOAD_SEEDS = {"mix256": 1002, "obst128": 1003, "mix3d64": 1004, "gauss32": N
 # eta_dot <= 1e-6 on the seed-1002 instance of this workload; converts the oracle's
 # seconds per iteration into solves/s in the reference arm.  Measured by this script's
 # own arm ("fp64" -> "iterations" in its JSON line).
-ORACLE_ITERS_PER_SOLVE = 11120
+ORACLE_ITERS_PER_SOLVE = {"mix256": 11120}   # the FP64 recurrence to eta <= 1e-6, checks every 10
 
 
 def parse():
@@ -401,20 +401,19 @@ def run_ours(args):
             out["mixed_vs_fp64"] = round(value / (1.0 / dt), 3)
 
     if not args.no_cpu and wl == WORKLOAD:
-        out["cpu_baseline"] = cpu_baseline(fp64_iters or (iters[0] if iters else None))
+        out["cpu_baseline"] = cpu_baseline(fp64_iters or (iters[0] if iters else None), wl)
     print(json.dumps(out))
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def oracle_seconds_per_iteration(n_iter: int):
-    """Time n_iter oracle iterations (plain FP64 C, OpenMP) on the seed-1002 instance."""
+def oracle_seconds_per_iteration(n_iter: int, wl: str = WORKLOAD):
+    """Time n_iter oracle iterations (plain FP64 C, OpenMP) on the workload's default instance."""
     import oracle as O
     from paper_2505_05424_gb300 import workloads as W
     O.build()
-    spec = W.MIX256
-    r0, r1, m = W.mixture_pair(spec, 1002)
+    spec, r0, r1, m = W.workload(wl)
     g = O.Grid(spec.D, spec.T, [spec.N] * spec.D)
     prob = O.Problem(g, r0, r1, m)
     st = O.State.zeros(g)
@@ -424,32 +423,33 @@ def oracle_seconds_per_iteration(n_iter: int):
     return (time.perf_counter() - t0) / n_iter
 
 
-def cpu_baseline(iters_per_solve):
+def cpu_baseline(iters_per_solve, wl: str = WORKLOAD):
     cores = len(os.sched_getaffinity(0))
-    spi = oracle_seconds_per_iteration(2)
+    spi = oracle_seconds_per_iteration(2, wl)
     val = (1.0 / (spi * iters_per_solve)) if iters_per_solve else None
     return {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"2 oracle iterations of {WORKLOAD} ({spi:.2f} s/iteration, OpenMP on {cores} threads); "
+            "sample": f"2 oracle iterations of {wl} ({spi:.2f} s/iteration, OpenMP on {cores} threads); "
                       f"solves/s = 1 / (s/iteration x {iters_per_solve} iterations to eta<=1e-6)"}
 
 
 def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    iters = ORACLE_ITERS_PER_SOLVE
-    for _ in range(args.warmup):
-        oracle_seconds_per_iteration(1)
-    per = [oracle_seconds_per_iteration(1) for _ in range(args.steps)]
-    spi = float(np.mean(per))
-    cores = len(os.sched_getaffinity(0))
+    wl = args.workload
+    iters = ORACLE_ITERS_PER_SOLVE.get(wl) if args.check_every == 10 else None
     if iters is None:
         print(json.dumps({"impl": "reference", "unavailable": "iterations-per-solve of the workload not recorded"}))
         return
+    for _ in range(args.warmup):
+        oracle_seconds_per_iteration(1, wl)
+    per = [oracle_seconds_per_iteration(1, wl) for _ in range(args.steps)]
+    spi = float(np.mean(per))
+    cores = len(os.sched_getaffinity(0))
     val = 1.0 / (spi * iters)
     out = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": spi * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESCS[WORKLOAD]}", "tol": args.tol},
+           "config": {"workload": f"{wl}: {WORKLOAD_DESCS.get(wl, wl)}", "tol": args.tol},
            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
                             "sample": f"each step = 1 oracle iteration; solves/s = 1/(s/it x {iters})"},
            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
