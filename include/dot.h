@@ -109,8 +109,10 @@ size_t dot_workspace_bytes(const dot_grid *grid, dot_precision prec);
  * workspace: device memory of at least dot_workspace_bytes() bytes, 256-byte
  * aligned, owned by the caller and kept alive until dot_destroy; NULL = the
  * library allocates (and frees) it itself.  stream: cudaStream_t to run on;
- * NULL = the legacy default stream.  The initial point is q = alpha = beta = 0,
- * sigma = sigma0 (0 lies in Q, Algorithm 1's input condition).
+ * NULL = the legacy default stream.  The context belongs to the CUDA device
+ * current at this call: every later call on it runs on that device and restores
+ * the caller's current device on return.  The initial point is q = alpha =
+ * beta = 0, sigma = sigma0 (0 lies in Q, Algorithm 1's input condition).
  * Returns DOT_EINVAL for bad shapes/densities, DOT_ENOMEM, or DOT_ECUDA. */
 int dot_create(const dot_grid *grid, const double *rho0, const double *rho1,
                const uint8_t *mask, const dot_options *opt, void *workspace,

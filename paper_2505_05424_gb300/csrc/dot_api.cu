@@ -174,7 +174,10 @@ struct dot_ctx {
   // is captured on (the caller's stream may be the legacy default stream, which
   // cannot be captured)
   cudaStream_t cap = nullptr;
+  int device = 0;           // the device of dot_create; made current by every entry point
 };
+
+int dot::context_device(const dot_ctx* c) { return c->device; }
 
 void dot::problem_of(const dot_ctx* c, dot_grid* g, dot_options* opt, void** stream, std::vector<double>* rho0,
                      std::vector<double>* rho1, std::vector<uint8_t>* mask, bool* has_mask) {
@@ -407,6 +410,8 @@ int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, con
   if (prepare_densities(g, rho0, rho1, mask, o.obstacle_weight, &c->m0, &c->m1, &c->omega, &any_mask, &why) !=
       DOT_OK)
     return fail(nullptr, DOT_EINVAL, why);
+  // the first device call: after every host-side check
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(nullptr, DOT_ECUDA, "no CUDA device");
   c->stream = (cudaStream_t)stream;
   size_t need = path_workspace_bytes(g, o.prec);
   if (workspace) {
@@ -451,6 +456,7 @@ int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, con
 
 int dot_solve(dot_ctx* c, double tol, long maxit) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   if (maxit < 0) return fail(c, DOT_EINVAL, "maxit must be >= 0");
   const auto t0 = std::chrono::steady_clock::now();
   const int ce = c->opt.check_every;
@@ -508,6 +514,7 @@ int dot_solve(dot_ctx* c, double tol, long maxit) {
 
 int dot_kkt(dot_ctx* c, double* kkt) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   int rc = compute_kkt(c);
   if (rc != DOT_OK) return rc;
   if (kkt) std::memcpy(kkt, c->kkt, sizeof(c->kkt));
@@ -516,6 +523,7 @@ int dot_kkt(dot_ctx* c, double* kkt) {
 
 int dot_get(dot_ctx* c, double* rho, double* m, double* phi, double* objective, double* kkt) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   const Geo& g = c->geo;
   if (objective || kkt) {
     int rc = compute_kkt(c);
@@ -541,6 +549,7 @@ int dot_get(dot_ctx* c, double* rho, double* m, double* phi, double* objective, 
 
 int dot_get_state(dot_ctx* c, double* q, double* alpha, double* beta, double* sigma, long* iters) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   std::string perr;
   int rc = c->path->read_state(q, alpha, beta, c->stream, &perr);
   if (rc != DOT_OK) return fail(c, rc, perr);
@@ -552,6 +561,7 @@ int dot_get_state(dot_ctx* c, double* q, double* alpha, double* beta, double* si
 int dot_set_state(dot_ctx* c, const double* q, const double* alpha, const double* beta, double sigma,
                   long iters) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   if (!q || !alpha || !beta) return fail(c, DOT_EINVAL, "q, alpha and beta are required");
   if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(c, DOT_EINVAL, "sigma must be > 0");
   std::string perr;
@@ -564,6 +574,7 @@ int dot_set_state(dot_ctx* c, const double* q, const double* alpha, const double
 
 int dot_poisson(dot_ctx* c, const double* b, double* phi) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   if (!b || !phi) return fail(c, DOT_EINVAL, "b and phi are required");
   std::string perr;
   LaunchCounter lc = counter(c);
@@ -576,6 +587,7 @@ int dot_poisson(dot_ctx* c, const double* b, double* phi) {
 
 int dot_profile(dot_ctx* c, int enable) {
   if (!c) return fail(nullptr, DOT_EINVAL, "ctx is NULL");
+  DeviceScope dev(c->device);
   DOT_CK(c, cudaStreamSynchronize(c->stream));
   if (c->prof) prof_flush(c);
   c->prof = enable != 0;
@@ -599,6 +611,7 @@ const char* dot_kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kKern
 
 void dot_destroy(dot_ctx* c) {
   if (!c) return;
+  DeviceScope dev(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);

@@ -251,6 +251,7 @@ extern "C" int dot_solve_multilevel(dot_ctx* ctx, int levels, double tol, double
     g_ml_err = "ctx is NULL";
     return DOT_EINVAL;
   }
+  DeviceScope dev(context_device(ctx));   // the coarse contexts live on the context's device
   dot_grid g;
   dot_options opt;
   std::vector<double> r0, r1;

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/dot.h"
 #include "dot_internal.cuh"
 
@@ -23,6 +25,24 @@ int prepare_densities(const Geo& g, const double* rho0, const double* rho1, cons
 // and the obstacle mask (cells whose weight is not 1).
 void problem_of(const dot_ctx* c, dot_grid* g, dot_options* opt, void** stream, std::vector<double>* rho0,
                 std::vector<double>* rho1, std::vector<uint8_t>* mask, bool* has_mask);
+// The device a context was created on; every entry point makes it current for
+// the duration of the call (DeviceScope) and restores the caller's device.
+int context_device(const dot_ctx* c);
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) == cudaSuccess && prev_ != dev && cudaSetDevice(dev) == cudaSuccess) set_ = true;
+  }
+  ~DeviceScope() {
+    if (set_) cudaSetDevice(prev_);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+
+ private:
+  int prev_ = 0;
+  bool set_ = false;
+};
 // Stopping measures of Sec. 5.3 (kkt[DOT_KKT_LEN]) from the reduction slots r;
 // cn2 = sum of squares of c.
 void kkt_measures(const Geo& g, double cn2, const double* r, long iters, double sigma, double* kkt);
