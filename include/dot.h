@@ -255,7 +255,9 @@ int dot_server_create(const dot_options *opt, const dot_server_options *sopt, do
 /* Queue a solve.  rho0, rho1, mask as for dot_create (copied before the call
  * returns); tol, maxit as for dot_solve; keep_fields: 1 = keep rho, m, phi for
  * dot_server_result, 0 = only the objective and the stopping measures.
- * *id receives the request id (> 0). */
+ * *id receives the request id (> 0).  Returns DOT_EINVAL for bad arguments and
+ * DOT_ENOMEM when a batch of one slot of this grid (dot_workspace_bytes-like
+ * footprint) exceeds the server's hbm_budget, so that it could never run. */
 int dot_server_submit(dot_server *srv, const dot_grid *grid, const double *rho0, const double *rho1,
                       const uint8_t *mask, double tol, long maxit, int keep_fields, long long *id);
 /* Wait up to timeout_s seconds (< 0: forever, 0: poll) for request id.  Returns

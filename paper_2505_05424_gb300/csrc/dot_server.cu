@@ -496,6 +496,11 @@ int dot_server_submit(dot_server* s, const dot_grid* grid, const double* rho0, c
   if (prepare_densities(r->geo, rho0, rho1, mask, s->opt.obstacle_weight, &r->m0, &r->m1, &r->omega, &r->has_mask,
                         &why) != DOT_OK)
     return sfail(s, DOT_EINVAL, why);
+  // a request that cannot fit the budget even in a batch of one slot would wait forever
+  const size_t need = MixedBatch::workspace_bytes(r->geo, 1, true);
+  if (need > s->sopt.hbm_budget)
+    return sfail(s, DOT_ENOMEM, "the request needs " + std::to_string(need) +
+                                    " bytes of workspace, more than the server's hbm_budget");
   for (double v : r->m0) r->cn2 += v * v;
   for (double v : r->m1) r->cn2 += v * v;
   r->tol = tol;

@@ -116,6 +116,16 @@ def test_admission_waits_for_memory():
         assert s["bytes"] <= budget
 
 
+def test_request_larger_than_the_budget_is_rejected():
+    # a 1 MB budget holds no batch of a 64^2 x 16 grid: DOT_ENOMEM at submit, not a
+    # request that waits forever
+    with DotServer(hbm_budget=1 << 20) as srv:
+        r0, r1, _ = instance(64, 16, 3800)
+        with pytest.raises(DotError):
+            srv.submit(2, 16, 64, r0, r1, tol=TOL, maxit=10)
+        assert srv.stats()["queued"] == 0
+
+
 def test_non_batchable_grid_and_errors():
     # N = 30 is not a multiple of 4: a batch of one slot on the SIMT passes
     st, res = solve_alone(30, 8, 3700)
