@@ -100,7 +100,7 @@ EXPORTS = ("dot_default_options", "dot_workspace_bytes", "dot_create", "dot_solv
            "dot_noalloc_last_error", "dot_server_default_options", "dot_server_create", "dot_server_submit",
            "dot_server_wait", "dot_server_result", "dot_server_release", "dot_server_stats",
            "dot_server_destroy", "dot_server_last_error", "dot_solve_multilevel", "dot_prolong_state",
-           "dot_multilevel_last_error")
+           "dot_multilevel_last_error", "dot_selftest_pipeline_timeout")
 
 _lib = None
 _lock = threading.Lock()
@@ -183,5 +183,7 @@ def load(build_if_missing: bool = True):
         lib.dot_prolong_state.restype = ctypes.c_int
         lib.dot_multilevel_last_error.argtypes = []
         lib.dot_multilevel_last_error.restype = ctypes.c_char_p
+        lib.dot_selftest_pipeline_timeout.argtypes = [ctypes.c_int, dp, P(ctypes.c_int)]
+        lib.dot_selftest_pipeline_timeout.restype = ctypes.c_int
         _lib = lib
         return lib

@@ -21,6 +21,34 @@ namespace dot {
 constexpr int kMaxD = 3;
 constexpr int kMaxK = 4 * kMaxD + 2;
 
+// Bounded wait on an mbarrier phase (shared-memory address `bar`): true once the
+// phase with the given parity has completed, false after about one second on the
+// global timer, so that a pipeline whose producer never arrives returns an error
+// status to the host instead of hanging the GPU.  The timer is read on the first
+// miss and then every 1024 polls.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0; it < 0x80000000u; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 1023u) == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (it == 0) t0 = t;
+      else if (t - t0 > kWaitLimitNs) return false;
+    }
+  }
+  return false;
+}
+
 // Unsigned division of n < 2^31 by a fixed divisor d >= 2 with one multiply-high
 // and a shift: with l = ceil(log2 d) and m = ceil(2^(31 + l) / d) (< 2^32),
 // floor(n / d) = umulhi(n, m) >> (l - 1) (the round-up method of Granlund and

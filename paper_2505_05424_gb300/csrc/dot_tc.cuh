@@ -35,6 +35,8 @@ struct TcPass {
   float2* accum;        // ROWS_A (nullable): add the result into this two-float field (same
                         // layout as out) instead of writing out
   int* err;             // set by a CTA whose pipeline wait timed out
+  unsigned extra_tx;    // self-test only (dot_selftest_pipeline_timeout): bytes each stage's
+                        // barrier expects beyond what its loads deliver; 0 otherwise
 };
 // Returns false when the pass cannot run on the tensor cores (unsupported K,
 // misaligned strides or pointers, tensor maps that cannot be encoded).

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <chrono>
 #include <cstdint>
 #include <cstring>
 
@@ -49,7 +50,6 @@ constexpr int kChunkK = 32;          // K elements per stage (128 bytes: one SW1
 constexpr int kStages = 2;
 constexpr int kMaxN = 256;           // columns of the accumulator (MMA N)
 constexpr int kThreadsTC = 192;
-constexpr unsigned kSpinLimit = 1u << 25;   // bounded mbarrier waits (well under a second of polling)
 
 constexpr int kXBytes = kTileM * kChunkK * 4;      // 16 KB
 // A stage holds the X tile (hi and lo) and Nout rows of the table (hi and lo);
@@ -82,19 +82,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Bounded wait for the phase with the given parity; returns false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  const uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return mbar_wait_bounded(smem_u32(bar), parity);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -167,6 +155,7 @@ struct PassArgs {
   FastDiv fP, fS[kMaxD], fN[kMaxD];
   float2* accum;   // ROWS_A: accumulate into a two-float field instead of writing out
   int* err;
+  unsigned extra_tx;   // see TcPass::extra_tx
 };
 
 __global__ void __launch_bounds__(kThreadsTC, 2)
@@ -233,7 +222,7 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
   const int nout = min(pa.Nout, (pa.K - n0 + 15) / 16 * 16);
   if (warp == 0) {
     if (lane == 0) {
-      const unsigned bytes = kXBytes + 2u * (unsigned)pa.Nout * kChunkK * 4u;
+      const unsigned bytes = kXBytes + 2u * (unsigned)pa.Nout * kChunkK * 4u + pa.extra_tx;
       for (int c = 0; c < nchunks; ++c) {
         const int s = c % kStages, it = c / kStages;
         if (c >= kStages && !mbar_wait(&empty[s], (it - 1) & 1)) { atomicExch(&s_fail, 1); break; }
@@ -476,6 +465,7 @@ bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
   pa.fA = make_fastdiv((unsigned)pa.A);
   pa.fM = make_fastdiv((unsigned)pa.M);
   pa.err = p.err;
+  pa.extra_tx = p.extra_tx;
   pa.accum = p.mode == TC_ROWS_A ? p.accum : nullptr;
   if (p.accum && p.mode != TC_ROWS_A) return false;
   if (p.mode == TC_ROWS_FLAT && (p.R % pa.A != 0 || pa.A % pa.M != 0 || pa.ldo < pa.M)) return false;
@@ -500,3 +490,57 @@ bool launch_tc_pass(const TcPass& p, cudaStream_t s) {
 }
 
 }  // namespace dot
+
+// Self-test of the bounded pipeline waits (include/dot_selftest.h).
+extern "C" int dot_selftest_pipeline_timeout(int inject, double* seconds, int* flag) {
+  using namespace dot;
+  if (!seconds || !flag) return -1;
+  const int K = 32, R = 128;   // one 128-row tile, one chunk: a single CTA
+  float *x = nullptr, *bh = nullptr, *bl = nullptr, *out = nullptr;
+  int* err = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaMalloc(&x, sizeof(float) * R * K);
+  if (e == cudaSuccess) e = cudaMalloc(&bh, sizeof(float) * K * K);
+  if (e == cudaSuccess) e = cudaMalloc(&bl, sizeof(float) * K * K);
+  if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float) * R * K);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(float) * R * K, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bh, 0, sizeof(float) * K * K, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bl, 0, sizeof(float) * K * K, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int rc = e == cudaSuccess ? 0 : -3;
+  if (rc == 0) {
+    TcPass p;
+    std::memset(&p, 0, sizeof(p));
+    p.X = x;
+    p.ldx = K;
+    p.Bhi = bh;
+    p.Blo = bl;
+    p.ldb = K;
+    p.out = out;
+    p.K = K;
+    p.mode = TC_ROWS_FLAT;
+    p.R = R;
+    p.A = R;
+    p.M = 1;
+    p.ldo = 1;
+    p.err = err;
+    // 16 bytes more than the loads deliver: the stage's barrier never completes
+    p.extra_tx = inject ? 16u : 0u;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!launch_tc_pass(p, s)) rc = -1;
+    if (rc == 0 && cudaStreamSynchronize(s) != cudaSuccess) rc = -3;
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rc == 0 && cudaMemcpy(flag, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = -3;
+  }
+  if (s) cudaStreamDestroy(s);
+  cudaFree(x);
+  cudaFree(bh);
+  cudaFree(bl);
+  cudaFree(out);
+  cudaFree(err);
+  return rc;
+}
+

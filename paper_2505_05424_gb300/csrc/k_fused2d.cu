@@ -444,7 +444,6 @@ constexpr int kOffW2 = kOffW1 + VNQ1 * 8;                 // [VNQ2] two-float
 constexpr int kOffBar = (kOffW2 + VNQ2 * 8 + 15) / 16 * 16;
 constexpr int kSmemV2 = kOffBar + 64;
 static_assert(kOffW1 % 16 == 0, "two-float face arrays are 16-byte aligned");
-constexpr unsigned kSpinV2 = 1u << 25;
 // 11 warps: one thread per cone of the 10 x 34 halo rectangle (256 owned + 84
 // ring cones), so phase A takes one round; 552 faces take two
 constexpr int kThreadsV2 = 352;
@@ -454,21 +453,7 @@ constexpr int kTchunkV2 = 16;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
-  const uint32_t a = sa(bar);
-  for (unsigned it = 0; it < kSpinV2; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) { return mbar_wait_bounded(sa(bar), parity); }
 
 __device__ __forceinline__ void issue_beta(const CUtensorMap* tm, float2* dst, uint64_t* bar, int y, int x, int t,
                                            int slot) {

@@ -1,4 +1,4 @@
-"""CPU checks of the C ABI: the library loads, exports every symbol include/dot.h
+"""CPU checks of the C ABI: the library loads, exports every symbol include/*.h
 declares, sizes its workspace and rejects bad arguments before touching the GPU."""
 import ctypes
 import os
@@ -19,7 +19,8 @@ def lib():
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "dot.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(dot_[a-z0-9_]+)\s*\(", text)))
 
