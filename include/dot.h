@@ -121,7 +121,10 @@ int dot_create(const dot_grid *grid, const double *rho0, const double *rho1,
 /* Run Algorithm 2 until eta_dot <= tol at a check (Sec. 5.3) or maxit more
  * iterations.  tol <= 0 never stops early.  Returns DOT_OK when converged,
  * DOT_ENOTCONV at maxit, DOT_ETIMEOUT, DOT_EDIVERGED or DOT_ECUDA.  Blocks the
- * calling thread at every check (it reads the stopping measures). */
+ * calling thread at every check (it reads the stopping measures).  With
+ * opt.use_graphs (DOT_MIXED, not under dot_profile) each whole check period is
+ * replayed from a CUDA graph captured on the first period; the results are the
+ * same bit for bit as with kernel-by-kernel launches. */
 int dot_solve(dot_ctx *ctx, double tol, long maxit);
 
 /* Results.  Any pointer may be NULL.  rho = alpha_0 / h_0 and m_d = alpha_d / h_0
@@ -153,7 +156,8 @@ int dot_poisson(dot_ctx *ctx, const double *b, double *phi);
  * later launch on this context bracketed by CUDA events recorded on the
  * context's stream; the elapsed times are accumulated per kernel id at every
  * synchronisation point (stopping-measure checks, end of dot_solve).
- * dot_profile(ctx, 0) stops.  dot_profile_read copies, for kernel ids
+ * dot_profile(ctx, 0) stops.  Profiled solves launch kernel by kernel (no graph
+ * replay), so that every kernel is bracketed.  dot_profile_read copies, for kernel ids
  * 0..max-1, the total milliseconds and launch counts; it returns the number of
  * kernel ids (DOT_NUM_KERNELS).  dot_kernel_name(id) names each id. */
 #define DOT_NUM_KERNELS 12
