@@ -282,6 +282,9 @@ int dot_server_stats(dot_server *srv, double *out, int n);
 /* Stops the server thread (queued and running requests are abandoned) and frees
  * every device buffer. */
 void dot_server_destroy(dot_server *srv);
+/* Message of the server's last failing call (or of the server thread's fatal
+ * error); with srv NULL, of the calling thread's last failing dot_server_create.
+ * The string stays valid until the calling thread's next call of this function. */
 const char *dot_server_last_error(const dot_server *srv);
 
 #ifdef __cplusplus

@@ -604,7 +604,14 @@ void dot_server_destroy(dot_server* s) {
 
 const char* dot_server_last_error(const dot_server* s) {
   if (!s) return g_srv_err.c_str();
-  return s->err.empty() ? s->fatal.c_str() : s->err.c_str();
+  // the server thread may set `fatal` at any time: copy under the lock into a
+  // buffer of the calling thread (valid until its next call)
+  thread_local std::string copy;
+  {
+    std::lock_guard<std::mutex> l(const_cast<dot_server*>(s)->mu);
+    copy = s->err.empty() ? s->fatal : s->err;
+  }
+  return copy.c_str();
 }
 
 }  // extern "C"
