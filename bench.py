@@ -340,7 +340,7 @@ def run_ours(args):
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0]) if v[1]}
 
     # e2e through the public API with host buffers: create (H2D) -> solve -> get (D2H)
-    e2e_lat = []
+    e2e_lat, e2e_iters = [], []
     h2d = d2h = 0
     for k in range(args.e2e_steps):
         r0, r1, m = instance(100 + k)
@@ -351,6 +351,7 @@ def run_ours(args):
         rho, mm, phi, obj, kk = s.dot_get()
         torch.cuda.synchronize()
         e2e_lat.append(time.perf_counter() - t0)
+        e2e_iters.append(int(kk["iterations"]))
         s.close()
         h2d = r0.nbytes + r1.nbytes + (0 if m is None else m.size)
         d2h = rho.nbytes + sum(a.nbytes for a in mm) + phi.nbytes + 8 * 12
@@ -373,7 +374,8 @@ def run_ours(args):
         "it_per_s": round(sum(iters) / (elapsed_ms / 1e3), 1),
         "clocks": clk, "gpu_launches": int(gpu_launches),
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "iterations": e2e_iters,
+                "seeds": f"{base_seed}+100+step" if base_seed is not None else None},
         "roofline": roof, "kernels": kernels,
     }
 
