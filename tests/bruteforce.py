@@ -105,3 +105,82 @@ class DenseDOT:
     def alpha_from(self, lam, q, omega):
         """alpha = (Lambda_0; (L_X^d L_T^*(omega Lambda_0)) o q_d) -- stationarity of (8)."""
         return [lam] + [(M.T @ (omega * lam)) * qd for M, qd in zip(self.M, q[1:])]
+
+
+class DenseSOC:
+    """Dense F (eq. (operatorF), (fdetails)), B (eq. (bdd), weighted by sqrt(omega/2) as for
+    P_omega in Sec. 5.4) and d for the SOCP reformulation (opt-dualsoc).
+
+    Written from the definitions by placing every cone and face at its space-time
+    position (index units: node (t, x), time face (t + 1/2, x), space face of axis d at
+    x_d + 1/2) and matching positions, so no index arithmetic is shared with the oracle.
+    F^d_v of the cone at (t + 1/2, x) is q_d at (t, x_d - 1/2), (t, x_d + 1/2),
+    (t + 1, x_d - 1/2), (t + 1, x_d + 1/2) for v = 1..4, and 0 where no such face exists.
+    Layouts follow the oracle's interface: q = (q_0; q_1; ..; q_D) with each block in
+    C order, cone vectors block-major (component, cone)."""
+
+    def __init__(self, D, T, N):
+        self.D, self.T, self.N = D, T, list(N)
+        self.K = 4 * D + 2
+        cone_shape = (T,) + tuple(N)
+        self.cone_pos = [(t + 0.5,) + tuple(float(v) for v in x)
+                         for t, *x in np.ndindex(*cone_shape)]
+        self.n0 = len(self.cone_pos)
+        # faces: family 0 are the cones' own time faces; family d has N_d - 1 faces along d
+        self.face_index = {}                   # (family, position) -> column of q
+        col = 0
+        for t, *x in np.ndindex(*cone_shape):
+            self.face_index[(0, (t + 0.5,) + tuple(float(v) for v in x))] = col
+            col += 1
+        for d in range(1, D + 1):
+            shape = [T + 1] + list(N)
+            shape[d] -= 1
+            for idx in np.ndindex(*shape):
+                pos = [float(v) for v in idx]
+                pos[d] += 0.5
+                self.face_index[(d, tuple(pos))] = col
+                col += 1
+        self.nq = col
+        self.F = np.zeros(((self.K - 1) * self.n0, self.nq))
+        for c, pos in enumerate(self.cone_pos):
+            self.F[c, self.face_index[(0, pos)]] = 1.0
+            for d in range(1, D + 1):
+                for v, (dt, dx) in enumerate(((-0.5, -0.5), (-0.5, 0.5), (0.5, -0.5), (0.5, 0.5))):
+                    src = list(pos)
+                    src[0] += dt
+                    src[d] += dx
+                    j = self.face_index.get((d, tuple(src)))
+                    if j is not None:
+                        self.F[(1 + 4 * (d - 1) + v) * self.n0 + c, j] = 1.0
+
+    def B(self, omega):
+        """x = (x_0; x_1..x_4D) per cone -> (-x_0; s x_1; ..; s x_4D; x_0), s = sqrt(omega/2)."""
+        n0, K = self.n0, self.K
+        s = np.sqrt(np.asarray(omega, dtype=float) / 2.0)
+        B = np.zeros((K * n0, (K - 1) * n0))
+        for c in range(n0):
+            B[c, c] = -1.0
+            for j in range(1, K - 1):
+                B[j * n0 + c, j * n0 + c] = s[c]
+            B[(K - 1) * n0 + c, c] = 1.0
+        return B
+
+    def d(self):
+        v = np.zeros(self.K * self.n0)
+        v[: self.n0] = 1.0
+        v[(self.K - 1) * self.n0:] = 1.0
+        return v
+
+    def cones_reading_face(self, d, face_pos):
+        """Cones whose F^d_v reads the space face at face_pos (explicit geometry: cone
+        times t - 1/2 and t + 1/2 of the face's time node t, cells x_d -+ 1/2 along d)."""
+        out = []
+        for dt in (-0.5, 0.5):
+            for dx in (-0.5, 0.5):
+                p = list(face_pos)
+                p[0] += dt
+                p[d] += dx
+                p = tuple(p)
+                if 0 < p[0] < self.T and all(0 <= p[a] <= self.N[a - 1] - 1 for a in range(1, self.D + 1)):
+                    out.append(self.cone_pos.index(p))
+        return out
