@@ -157,7 +157,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---- algorithmic bytes ("Kernels and their rooflines") --------
+# ---- algorithmic bytes of one launch per kernel ---------------------------------
 
 def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
     """Compulsory DRAM bytes of one launch of `name` (natural, unpadded counts)."""
@@ -187,9 +187,26 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
     return float(table.get(name, 0.0))
 
 
-# DRAM bytes (read + write) of one launch, from an ncu capture of the mix256 workload
-# (profiles/k_fused2d_tma_mix256.md); valid while the kernel is unchanged since.
-NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"): 597.195264e6 + 475.236096e6}
+# DRAM bytes (read + write) of one launch from a stored ncu capture of the kernel on
+# the named workload, with the SHA-256 prefix of the kernel source it was taken on:
+# the figure is reported only while that source is unchanged (else traffic = null).
+NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"):
+               (597.195264e6 + 475.236096e6, "k_fused2d.cu", "2e517d2654914088")}
+
+
+def stored_traffic(kernel: str, workload: str, prec: str):
+    """(bytes, note) of the stored ncu DRAM traffic, or (None, reason)."""
+    import hashlib
+    ent = NCU_TRAFFIC.get((kernel, workload, prec))
+    if ent is None:
+        return None, "no stored ncu capture for this kernel and workload"
+    nbytes, src, sha = ent
+    path = os.path.join(ROOT, "paper_2505_05424_gb300", "csrc", src)
+    with open(path, "rb") as fh:
+        cur = hashlib.sha256(fh.read()).hexdigest()[:16]
+    if cur != sha:
+        return None, f"{src} changed since the stored ncu capture"
+    return nbytes, f"stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), {src} sha256 {sha}"
 
 
 # ---- replicas: one process per GPU, independent solves, no data-path collective --
@@ -326,9 +343,10 @@ def run_ours(args):
     else:
         achieved = abytes / (per_launch_ms / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
-        traffic = NCU_TRAFFIC.get((dname, wl, args.prec))
+        traffic, traffic_src = stored_traffic(dname, wl, args.prec)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": dname,
+                "frac": round(achieved / hbm, 4), "traffic": traffic, "traffic_source": traffic_src,
+                "kernel": dname,
                 "per_launch_ms": round(per_launch_ms, 5), "algorithmic_bytes": abytes,
                 "peak_source": f"{peak_src} (of measured copy bandwidth)" if peak_src == "measured" else peak_src}
 

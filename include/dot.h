@@ -166,10 +166,10 @@ int dot_profile_read(dot_ctx *ctx, double *ms_total, long *launches, int max);
 const char *dot_kernel_name(int id);
 
 /* Refined Poisson solve for callers that cannot allocate device memory (no
- * counterpart in the paper; it serves code that runs inside a fixed memory plan,
- * such as a stream being captured into a CUDA graph, hosts that forbid allocation
- * on their worker threads, or processes whose device memory is reserved by
- * another allocator).  It computes what dot_poisson computes for a DOT_MIXED
+ * counterpart in the paper; it serves plugins of hosts that forbid allocation on
+ * their worker threads, processes whose device memory is reserved by another
+ * allocator, and loops with a fixed memory budget that must not risk an
+ * allocation failing part way through).  It computes what dot_poisson computes for a DOT_MIXED
  * context -- phi = (A^*A)^dagger b by FP32/3xTF32 DCT solves with one refinement
  * step -- on caller-owned device buffers, and allocates nothing: all scratch
  * lives in one fixed __device__ array of the library (about 31 MB, held by every
@@ -177,8 +177,9 @@ const char *dot_kernel_name(int id);
  *   b    : device, FP32, [T+1][N_1]...[N_D]           (read only)
  *   phi  : device, 2 floats per node (hi, lo) in the same order; phi = hi + lo
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
- * Limits: D in {2, 3}, T+1 and every N_d in [2, 256], (T+1) N_1...N_D <= 2^20
- * nodes; larger grids return DOT_EINVAL with a message from
+ * Limits: D in {2, 3}, T+1 in [2, 160] (the time axis runs the SIMT time pass,
+ * built for at most 160 time nodes, as in DOT_MIXED contexts), every N_d in
+ * [2, 256], (T+1) N_1...N_D <= 2^20 nodes; larger grids return DOT_EINVAL with a message from
  * dot_noalloc_last_error().  The first call on a device fetches the array's
  * device address and should come before any stream capture.  Every call shares
  * the array: calls whose work overlaps on the GPU race and must be serialised. */

@@ -1,10 +1,11 @@
 // dot_noalloc.cu -- the mixed-precision refined Poisson solve for callers that
 // cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc or any allocating runtime: code that runs
-// while a CUDA graph is being captured into a fixed memory plan, plugins of hosts
-// that forbid allocation on their worker threads, or processes whose device memory
-// is already fully reserved by another allocator.  dot_poisson_f32_noalloc serves
+// Some callers cannot call cudaMalloc or any allocating runtime: plugins of hosts
+// that forbid allocation on their worker threads, processes whose device memory
+// is already fully reserved by another allocator, and loops with a fixed memory
+// budget that must not risk an allocation failing part way through a run.
+// dot_poisson_f32_noalloc serves
 // them: the caller passes the right-hand side and the output buffer, and every
 // scratch buffer the solve needs (four node-sized FP32 fields, the FP64 partial
 // sums of the zero mode, the DCT tables and the pipeline error flag) lives in one
@@ -30,7 +31,10 @@ namespace dot {
 namespace {
 
 constexpr long long kMaxNodes = 1LL << 20;  // (T+1) * N_1 * ... * N_D
-constexpr int kMaxAxis = 256;               // largest node count along one axis
+constexpr int kMaxAxis = 256;               // largest node count along one spatial axis
+// Here the time axis runs the SIMT time pass of the mixed path (no padded time
+// tables), which is built for at most 160 time nodes, as DOT_MIXED contexts are.
+constexpr int kMaxTimeNodes = 160;
 
 // Layout of the scratch array (256-byte aligned pieces, sizes in bytes).
 constexpr size_t kField = (size_t)kMaxNodes * sizeof(float);
@@ -86,7 +90,7 @@ extern "C" int dot_poisson_f32_noalloc(const dot_grid* grid, const float* b, flo
   using namespace dot;
   if (!grid || !b || !phi) return fail(DOT_EINVAL, "grid, b and phi are required");
   if (grid->D != 2 && grid->D != 3) return fail(DOT_EINVAL, "D must be 2 or 3");
-  if (grid->T < 1 || grid->T + 1 > kMaxAxis) return fail(DOT_EINVAL, "T + 1 must lie in [2, 256]");
+  if (grid->T < 1 || grid->T + 1 > kMaxTimeNodes) return fail(DOT_EINVAL, "T + 1 must lie in [2, 160]");
   long long nn = grid->T + 1;
   for (int d = 0; d < grid->D; ++d) {
     if (grid->N[d] < 2 || grid->N[d] > kMaxAxis) return fail(DOT_EINVAL, "every N[d] must lie in [2, 256]");
