@@ -471,16 +471,19 @@ __device__ __forceinline__ float2 bt(const float2* tile, int c, int xh, int yh) 
   return tile[(c * VHX + xh) * VBW + yh + 1];
 }
 
-// z components 1..8 of a halo cone into the tiles: 1, 2, 5, 6 -> ztn; 3, 4, 7, 8 -> ztp
-__device__ __forceinline__ void put_z(float (*ztn)[VNH], float (*ztp)[VNH], int hc, const float2* z) {
-  ztn[0][hc] = ff_round(z[1]);
-  ztn[1][hc] = ff_round(z[2]);
-  ztn[2][hc] = ff_round(z[5]);
-  ztn[3][hc] = ff_round(z[6]);
-  ztp[0][hc] = ff_round(z[3]);
-  ztp[1][hc] = ff_round(z[4]);
-  ztp[2][hc] = ff_round(z[7]);
-  ztp[3][hc] = ff_round(z[8]);
+// z components 1..8 of a halo cone into the tiles, from the lane pairs of
+// ff2_proj_soc10: (1, 2), (5, 6) -> ztn; (3, 4), (7, 8) -> ztp
+__device__ __forceinline__ void put_z(float (*ztn)[VNH], float (*ztp)[VNH], int hc, const ff2* P) {
+  const float2 r1 = add2(P[1].h, P[1].l), r2 = add2(P[2].h, P[2].l);
+  const float2 r3 = add2(P[3].h, P[3].l), r4 = add2(P[4].h, P[4].l);
+  ztn[0][hc] = r1.x;
+  ztn[1][hc] = r1.y;
+  ztn[2][hc] = r3.x;
+  ztn[3][hc] = r3.y;
+  ztp[0][hc] = r2.x;
+  ztp[1][hc] = r2.y;
+  ztp[2][hc] = r4.x;
+  ztp[3][hc] = r4.y;
 }
 __device__ __forceinline__ void put_z0(float (*ztn)[VNH], float (*ztp)[VNH], int hc) {
 #pragma unroll
@@ -489,33 +492,82 @@ __device__ __forceinline__ void put_z0(float (*ztn)[VNH], float (*ztp)[VNH], int
     ztp[v][hc] = 0.f;
   }
 }
-// z of cone (t, x, y) from the iteration-k q (global) and a beta tile, in two-float
-// arithmetic as cone_z; false for a cone outside the grid.
-__device__ __forceinline__ bool cone_z_tile(const Geo& g, const FusedArgs& a, const float2* tile, int t, int x,
-                                            int y, int xh, int yh, float2* z) {
-  if (x < 0 || y < 0 || x >= g.N[0] || y >= g.N[1]) return false;
-  const int P = (int)g.P, N1 = g.N[1];
-  const int i = t * P + x * N1 + y;
-  const float* q1 = a.q[1];
-  const float* q2 = a.q[2];
+// The q^k values a cone (t, x, y) reads: q_0 at the cone, and the q_1, q_2 faces on
+// either side of it on time nodes t (v = 1, 2) and t+1 (v = 3, 4), zero where F
+// has no source face.  A thread keeps its cone column for all cone times, and the
+// node-(t+1) values of cone t are the node-t values of cone t+1, so per cone time
+// it loads q_0 and the node-(t+1) pairs only.
+struct ConeQ {
+  float x0;
+  float2 xb, xd;   // (q_1 left, right), (q_2 left, right) on node t+1
+};
+__device__ __forceinline__ void load_cone_q(const Geo& g, const FusedArgs& a, int t, int x, int y, ConeQ* c) {
+  const int P_ = (int)g.P, N1 = g.N[1];
+  const int i = t * P_ + x * N1 + y;
   const bool xl = x >= 1, xr = x <= g.N[0] - 2, yl = y >= 1, yr = y <= g.N[1] - 2;
-  float xv[K2 - 1];
-  xv[0] = a.q[0][i];
-  xv[1] = xl ? q1[i - N1] : 0.f;
-  xv[2] = xr ? q1[i] : 0.f;
-  xv[3] = xl ? q1[i + P - N1] : 0.f;
-  xv[4] = xr ? q1[i + P] : 0.f;
-  xv[5] = yl ? q2[i - 1] : 0.f;
-  xv[6] = yr ? q2[i] : 0.f;
-  xv[7] = yl ? q2[i + P - 1] : 0.f;
-  xv[8] = yr ? q2[i + P] : 0.f;
-  const float s = a.somega ? a.somega[x * N1 + y] : 0.70710678118654752f;
-  z[0] = ff_add(two_sum(-xv[0], 1.f), ff_neg(bt(tile, 0, xh, yh)));
-#pragma unroll
-  for (int j = 1; j < K2 - 1; ++j) z[j] = ff_add(two_prod(s, xv[j]), ff_neg(bt(tile, j, xh, yh)));
-  z[K2 - 1] = ff_add(two_sum(xv[0], 1.f), ff_neg(bt(tile, K2 - 1, xh, yh)));
-  ff_proj_soc<K2>(z);
-  return true;
+  c->x0 = a.q[0][i];
+  c->xb = make_float2(xl ? a.q[1][i + P_ - N1] : 0.f, xr ? a.q[1][i + P_] : 0.f);
+  c->xd = make_float2(yl ? a.q[2][i + P_ - 1] : 0.f, yr ? a.q[2][i + P_] : 0.f);
+}
+// the node-t pairs (at the first cone time of a chunk)
+__device__ __forceinline__ void load_cone_q_node(const Geo& g, const FusedArgs& a, int t, int x, int y, float2* xa,
+                                                 float2* xc) {
+  const int P_ = (int)g.P, N1 = g.N[1];
+  const int i = t * P_ + x * N1 + y;
+  const bool xl = x >= 1, xr = x <= g.N[0] - 2, yl = y >= 1, yr = y <= g.N[1] - 2;
+  *xa = make_float2(xl ? a.q[1][i - N1] : 0.f, xr ? a.q[1][i] : 0.f);
+  *xc = make_float2(yl ? a.q[2][i - 1] : 0.f, yr ? a.q[2][i] : 0.f);
+}
+// z of a cone from its q^k values and its beta tile entries, in two-float
+// arithmetic, as five lane pairs P[0] = (z_0, z_9), P[k] = (z_{2k-1}, z_{2k}).
+__device__ __forceinline__ void cone_z(float x0, float2 xa, float2 xb, float2 xc, float2 xd, float s,
+                                       const float2* tile, int xh, int yh, ff2* P) {
+  const float2 s2 = make_float2(s, s);
+  // y = B F q + d - beta/sigma: (1 - x_0, s x_1, ..., s x_8, 1 + x_0) - beta/sigma
+  P[0] = ff2_add(two_sum2(make_float2(-x0, x0), make_float2(1.f, 1.f)),
+                 ff2_neg(ff2_pack(bt(tile, 0, xh, yh), bt(tile, K2 - 1, xh, yh))));
+  P[1] = ff2_add(two_prod2(s2, xa), ff2_neg(ff2_pack(bt(tile, 1, xh, yh), bt(tile, 2, xh, yh))));
+  P[2] = ff2_add(two_prod2(s2, xb), ff2_neg(ff2_pack(bt(tile, 3, xh, yh), bt(tile, 4, xh, yh))));
+  P[3] = ff2_add(two_prod2(s2, xc), ff2_neg(ff2_pack(bt(tile, 5, xh, yh), bt(tile, 6, xh, yh))));
+  P[4] = ff2_add(two_prod2(s2, xd), ff2_neg(ff2_pack(bt(tile, 7, xh, yh), bt(tile, 8, xh, yh))));
+  ff2_proj_soc10(P);
+}
+
+__device__ __forceinline__ float2 grad_of(float2 a, float2 b, float invh) {
+  const float2 dh = two_sum(b.x, -a.x);
+  const float dl = (b.y - a.y) + dh.y;
+  return make_float2(dh.x * invh, dl * invh);
+}
+
+// One space face's update (line 4-5 of Algorithm 2 for q_d, alpha_d at one face):
+// rhs = A_d phi + alpha/sigma + sum over the cones reading the face of
+// s (z + beta/sigma), q = rhs / (1 + sum s^2), alpha/sigma += tau (A_d phi - q).
+// Returns q; *w = q - alpha/sigma - A_d phi (the next residual's face term).
+__device__ __forceinline__ float face_update(float2 gp, float2 al, bool has_now, bool has_prev, float2 bnr,
+                                             float2 bnl, float2 bpr, float2 bpl, float znr, float znl, float zpr,
+                                             float zpl, float sr, float sl, float ts, float2* alnew, float2* w) {
+  ff_acc acc = acc_init(gp);
+  acc_add(acc, al);
+  float zs = 0.f, dg = 0.f;
+  if (has_now) {
+    acc_add_mul(acc, bnr, sr);
+    acc_add_mul(acc, bnl, sl);
+    zs += sr * znr + sl * znl;
+    dg += sr * sr + sl * sl;
+  }
+  if (has_prev) {
+    acc_add_mul(acc, bpr, sr);
+    acc_add_mul(acc, bpl, sl);
+    zs += sr * zpr + sl * zpl;
+    dg += sr * sr + sl * sl;
+  }
+  acc_add_f(acc, zs);
+  const float den = 1.f + dg;
+  const float qv = ff_round(ff_div_f_r(acc_get(acc), den, __frcp_rn(den)));
+  const float gm = grad_minus(gp, qv);
+  *alnew = ff_add_f(al, ts * gm);
+  *w = ff_add_f(ff_neg(*alnew), -gm);
+  return qv;
 }
 
 __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const __grid_constant__ CUtensorMap tmb, Geo g,
@@ -549,6 +601,40 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
   const int tstart = ta > 0 ? ta - 1 : 0;
   const int tlast_cone = min(tb, g.T - 1);      // last cone time whose beta tile is loaded
 
+  // this thread's cone column: its owned cone, or one of the 84 halo-ring cones
+  // (threads 256..339); the same for every cone time
+  int cxh = -1, cyh = -1;
+  if (owner) {
+    cxh = lx + 1;
+    cyh = ly + 1;
+  } else if (tid < VNH) {
+    int r = tid - VX * VY;
+    if (r < VHY) { cxh = 0; cyh = r; }
+    else if ((r -= VHY) < VHY) { cxh = VHX - 1; cyh = r; }
+    else if ((r -= VHY) < VHX - 2) { cxh = 1 + r; cyh = 0; }
+    else { r -= VHX - 2; cxh = 1 + r; cyh = VHY - 1; }
+  }
+  const int cx = x0 - 1 + cxh, cy = y0 - 1 + cyh, chc = cxh * VHY + cyh;
+  const bool cone_ok = cxh >= 0 && cx >= 0 && cy >= 0 && cx < g.N[0] && cy < g.N[1];
+  const float cs = (cone_ok && a.somega) ? a.somega[cx * N1 + cy] : s_def;
+  // q^k of the cone column (node-t pairs and the next cone time's values), and the
+  // owner's potential on node t and alpha_0 / sigma of its cone, loaded a step ahead
+  float2 xa = make_float2(0.f, 0.f), xc = make_float2(0.f, 0.f);
+  ConeQ cq;
+  cq.x0 = 0.f;
+  cq.xb = cq.xd = make_float2(0.f, 0.f);
+  float2 ph_t = make_float2(0.f, 0.f), ph_n = make_float2(0.f, 0.f), al0 = make_float2(0.f, 0.f);
+  if (cone_ok && tstart <= g.T - 1) {
+    load_cone_q_node(g, a, tstart, cx, cy, &xa, &xc);
+    load_cone_q(g, a, tstart, cx, cy, &cq);
+    if (owner && tstart < tb) {
+      const int i = tstart * P + xo * N1 + yo;
+      ph_t = a.phi[i];
+      ph_n = a.phi[i + P];
+      al0 = a.al[0][i];
+    }
+  }
+
   if (tid == 0) {
     for (int b = 0; b < 3; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sa(&bars[b])));
@@ -562,8 +648,12 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
     inflight[tstart % 3] = true;
   }
 
-  float zc[K2], zp[K2];
-  float q0c = 0.f, q0p = 0.f, socp = 0.f;
+  // FP32 z of the owned cone at times t (zc) and t-1 (zp), lane pairs as ff2_proj_soc10
+  float2 zc[5], zp[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) zc[k] = zp[k] = make_float2(0.f, 0.f);
+  float q0c = 0.f, q0p = 0.f;
+  float2 socp = make_float2(0.f, 0.f);
   float2 w0c = make_float2(0.f, 0.f), w0p = make_float2(0.f, 0.f);   // q_0 - alpha_0/sigma - A_0 phi, cones t, t-1
   bool failed = false;
 
@@ -583,46 +673,49 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
       }
     }
     // ---------------- A: cones at time t ----------------
-    if (t <= g.T - 1) {
-      if (owner) {
-        const int xh = lx + 1, yh = ly + 1, hc = xh * VHY + yh;
-        float2 z[K2];
-        if (own_ok && cone_z_tile(g, a, tcur, t, xo, yo, xh, yh, z)) {
-          put_z(ztn, ztp[lev], hc, z);
-          // the cone before the chunk (t = ta - 1) is updated for the residual only
-          if (t < tb) {
-            const int i = t * P + xo * N1 + yo;
-            const float2 gp = grad_pair(a.phi, i, i + P, ih0);
-            const float2 al = a.al[0][i];
-            const float2 db = ff_add(bt(tcur, K2 - 1, xh, yh), ff_neg(bt(tcur, 0, xh, yh)));
-            float2 rhs = ff_add(gp, ff_add(al, db));
-            rhs = ff_add(rhs, ff_add(z[K2 - 1], ff_neg(z[0])));
-            const float qn = ff_round(ff_div_f(rhs, 3.f));
-            const float2 aln = ff_add_f(al, ts * grad_minus(gp, qn));
-            if (t >= ta) {
-              a.qn[0][i] = qn;
-              a.aln[0][i] = aln;
-            }
-            q0c = qn;
-            w0c = ff_add(ff_add_f(ff_neg(aln), qn), ff_neg(gp));   // q - alpha/sigma - A phi
+    if (t <= g.T - 1 && cxh >= 0) {
+      if (cone_ok) {
+        ff2 z[5];
+        cone_z(cq.x0, xa, cq.xb, xc, cq.xd, cs, tcur, cxh, cyh, z);
+        put_z(ztn, ztp[lev], chc, z);
+        // the cone before the chunk (t = ta - 1) is updated for the residual only
+        if (owner && t < tb) {
+          const int i = t * P + xo * N1 + yo;
+          const float2 gp = grad_of(ph_t, ph_n, ih0);
+          const float2 al = al0;
+          // q_0 (diagonal 3): rhs = A_0 phi + alpha_0/sigma + u_9 - u_0 with
+          // u = z + beta/sigma (F^*B^* of components 0 and K-1)
+          const ff2 u = ff2_add(z[0], ff2_pack(bt(tcur, 0, cxh, cyh), bt(tcur, K2 - 1, cxh, cyh)));
+          ff_acc acc = acc_init(gp);
+          acc_add(acc, al);
+          acc_add(acc, ff2_lane1(u));
+          acc_add(acc, ff_neg(ff2_lane0(u)));
+          const float qn = ff_round(ff_div_f_r(acc_get(acc), 3.f, 1.f / 3.f));
+          const float gm = grad_minus(gp, qn);
+          const float2 aln = ff_add_f(al, ts * gm);
+          if (t >= ta) {
+            a.qn[0][i] = qn;
+            a.aln[0][i] = aln;
           }
-#pragma unroll
-          for (int j = 0; j < K2; ++j) zc[j] = ff_round(z[j]);
-        } else {
-          put_z0(ztn, ztp[lev], hc);
+          q0c = qn;
+          w0c = ff_add_f(ff_neg(aln), -gm);   // q - alpha/sigma - A phi
+          // the next cone time's potential and alpha_0 / sigma
+          ph_t = ph_n;
+          if (t + 1 < tb) {
+            ph_n = a.phi[i + 2 * P];
+            al0 = a.al[0][i + P];
+          }
         }
-      }
-      // the 84 halo-ring cones, one per thread 256..339
-      else if (tid < VNH) {
-        int r = tid - VX * VY, xh, yh;
-        if (r < VHY) { xh = 0; yh = r; }
-        else if ((r -= VHY) < VHY) { xh = VHX - 1; yh = r; }
-        else if ((r -= VHY) < VHX - 2) { xh = 1 + r; yh = 0; }
-        else { r -= VHX - 2; xh = 1 + r; yh = VHY - 1; }
-        const int hc = xh * VHY + yh;
-        float2 z[K2];
-        if (cone_z_tile(g, a, tcur, t, x0 - 1 + xh, y0 - 1 + yh, xh, yh, z)) put_z(ztn, ztp[lev], hc, z);
-        else put_z0(ztn, ztp[lev], hc);
+        if (owner) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) zc[k] = add2(z[k].h, z[k].l);
+        }
+        // the next cone time's q^k: node t+1 pairs move down, the rest is loaded now
+        xa = cq.xb;
+        xc = cq.xd;
+        if (t + 1 <= tlast_cone) load_cone_q(g, a, t + 1, cx, cy, &cq);
+      } else {
+        put_z0(ztn, ztp[lev], chc);
       }
     }
     if (__syncthreads_or(!ok)) { failed = true; break; }
@@ -637,38 +730,28 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
     const bool write_node = t >= ta && ((t < tb) || (last_chunk && t == g.T));
     if (t >= ta) {
       const bool has_now = t <= g.T - 1, has_prev = t >= 1;
+      const float2 z2 = make_float2(0.f, 0.f);
       for (int e = tid; e < VNQ1 + VNQ2; e += kThreadsV2) {
         if (e < VNQ1) {
           const int jx = e / VY, yy = e % VY;
           const int j = x0 - 1 + jx, y = y0 + yy;
           float qv = 0.f;
-          float2 wv = make_float2(0.f, 0.f);
+          float2 wv = z2;
           if (j >= 0 && j <= g.N[0] - 2 && y < g.N[1]) {
             const int i = t * P + j * N1 + y;
-            const float2 gp = grad_pair(a.phi, i, i + N1, ih1);
             const int xr = jx + 1, xl = jx, yh = yy + 1;
             const float sr = a.somega ? a.somega[(j + 1) * N1 + y] : s_def;
             const float sl = a.somega ? a.somega[j * N1 + y] : s_def;
-            float2 mb = a.al[1][i];
-            float zs = 0.f, dg = 0.f;
-            if (has_now) {
-              mb = ff_add(mb, ff_add(ff_mul_f(bt(tcur, 1, xr, yh), sr), ff_mul_f(bt(tcur, 2, xl, yh), sl)));
-              zs += sr * ztn[0][xr * VHY + yh] + sl * ztn[1][xl * VHY + yh];
-              dg += sr * sr + sl * sl;
-            }
-            if (has_prev) {
-              mb = ff_add(mb, ff_add(ff_mul_f(bt(tprev, 3, xr, yh), sr), ff_mul_f(bt(tprev, 4, xl, yh), sl)));
-              zs += sr * ztp[lp][0][xr * VHY + yh] + sl * ztp[lp][1][xl * VHY + yh];
-              dg += sr * sr + sl * sl;
-            }
-            const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
-            qv = ff_round(ff_div_f(rhs, 1.f + dg));
-            const float2 aln = ff_add_f(a.al[1][i], ts * grad_minus(gp, qv));
+            float2 aln;
+            qv = face_update(grad_pair(a.phi, i, i + N1, ih1), a.al[1][i], has_now, has_prev,
+                             has_now ? bt(tcur, 1, xr, yh) : z2, has_now ? bt(tcur, 2, xl, yh) : z2,
+                             has_prev ? bt(tprev, 3, xr, yh) : z2, has_prev ? bt(tprev, 4, xl, yh) : z2,
+                             ztn[0][xr * VHY + yh], ztn[1][xl * VHY + yh], ztp[lp][0][xr * VHY + yh],
+                             ztp[lp][1][xl * VHY + yh], sr, sl, ts, &aln, &wv);
             if (write_node && jx >= 1) {
               a.qn[1][i] = qv;
               a.aln[1][i] = aln;
             }
-            wv = ff_add(ff_add_f(ff_neg(aln), qv), ff_neg(gp));   // q - alpha/sigma - A phi
           }
           sq1[lev][e] = qv;
           sw1[e] = wv;
@@ -677,33 +760,22 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
           const int xx = f / (VY + 1), jy = f % (VY + 1);
           const int x = x0 + xx, j = y0 - 1 + jy;
           float qv = 0.f;
-          float2 wv = make_float2(0.f, 0.f);
+          float2 wv = z2;
           if (x < g.N[0] && j >= 0 && j <= g.N[1] - 2) {
             const int i = t * P + x * N1 + j;
-            const float2 gp = grad_pair(a.phi, i, i + 1, ih2);
             const int xh = xx + 1, yr = jy + 1, yl = jy;
             const float sr = a.somega ? a.somega[x * N1 + j + 1] : s_def;
             const float sl = a.somega ? a.somega[x * N1 + j] : s_def;
-            float2 mb = a.al[2][i];
-            float zs = 0.f, dg = 0.f;
-            if (has_now) {
-              mb = ff_add(mb, ff_add(ff_mul_f(bt(tcur, 5, xh, yr), sr), ff_mul_f(bt(tcur, 6, xh, yl), sl)));
-              zs += sr * ztn[2][xh * VHY + yr] + sl * ztn[3][xh * VHY + yl];
-              dg += sr * sr + sl * sl;
-            }
-            if (has_prev) {
-              mb = ff_add(mb, ff_add(ff_mul_f(bt(tprev, 7, xh, yr), sr), ff_mul_f(bt(tprev, 8, xh, yl), sl)));
-              zs += sr * ztp[lp][2][xh * VHY + yr] + sl * ztp[lp][3][xh * VHY + yl];
-              dg += sr * sr + sl * sl;
-            }
-            const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
-            qv = ff_round(ff_div_f(rhs, 1.f + dg));
-            const float2 aln = ff_add_f(a.al[2][i], ts * grad_minus(gp, qv));
+            float2 aln;
+            qv = face_update(grad_pair(a.phi, i, i + 1, ih2), a.al[2][i], has_now, has_prev,
+                             has_now ? bt(tcur, 5, xh, yr) : z2, has_now ? bt(tcur, 6, xh, yl) : z2,
+                             has_prev ? bt(tprev, 7, xh, yr) : z2, has_prev ? bt(tprev, 8, xh, yl) : z2,
+                             ztn[2][xh * VHY + yr], ztn[3][xh * VHY + yl], ztp[lp][2][xh * VHY + yr],
+                             ztp[lp][3][xh * VHY + yl], sr, sl, ts, &aln, &wv);
             if (write_node && jy >= 1) {
               a.qn[2][i] = qv;
               a.aln[2][i] = aln;
             }
-            wv = ff_add(ff_add_f(ff_neg(aln), qv), ff_neg(gp));   // q - alpha/sigma - A phi
           }
           sq2[lev][f] = qv;
           sw2[f] = wv;
@@ -715,30 +787,33 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
     if (own_ok && t - 1 >= ta && t - 1 < tb) {
       const int i = (t - 1) * P + xo * N1 + yo;
       const bool xl = xo >= 1, xr = xo <= g.N[0] - 2, yl = yo >= 1, yr = yo <= g.N[1] - 2;
-      float xv[K2 - 1];
-      xv[0] = q0p;
-      xv[1] = xl ? sq1[lp][lx * VY + ly] : 0.f;
-      xv[2] = xr ? sq1[lp][(lx + 1) * VY + ly] : 0.f;
-      xv[3] = xl ? sq1[lev][lx * VY + ly] : 0.f;
-      xv[4] = xr ? sq1[lev][(lx + 1) * VY + ly] : 0.f;
-      xv[5] = yl ? sq2[lp][lx * (VY + 1) + ly] : 0.f;
-      xv[6] = yr ? sq2[lp][lx * (VY + 1) + ly + 1] : 0.f;
-      xv[7] = yl ? sq2[lev][lx * (VY + 1) + ly] : 0.f;
-      xv[8] = yr ? sq2[lev][lx * (VY + 1) + ly + 1] : 0.f;
+      const float2 xa = make_float2(xl ? sq1[lp][lx * VY + ly] : 0.f, xr ? sq1[lp][(lx + 1) * VY + ly] : 0.f);
+      const float2 xb = make_float2(xl ? sq1[lev][lx * VY + ly] : 0.f, xr ? sq1[lev][(lx + 1) * VY + ly] : 0.f);
+      const float2 xc = make_float2(yl ? sq2[lp][lx * (VY + 1) + ly] : 0.f, yr ? sq2[lp][lx * (VY + 1) + ly + 1] : 0.f);
+      const float2 xd = make_float2(yl ? sq2[lev][lx * (VY + 1) + ly] : 0.f, yr ? sq2[lev][lx * (VY + 1) + ly + 1] : 0.f);
       const float s = a.somega ? a.somega[xo * N1 + yo] : s_def;
       const int xh = lx + 1, yh = ly + 1;
-      float inc = (zp[0] - 1.f) + xv[0];
-      socp = fmaf(inc, inc, socp);
-      a.betan[i] = ff_add_f(bt(tprev, 0, xh, yh), ts * inc);
+      const float2 ns2 = make_float2(-s, -s), ts2 = make_float2(ts, ts);
+      // increments z - B F q^{k+1} - d, lane pairs as zp
+      float2 inc[5];
+      inc[0] = add2(sub2(zp[0], make_float2(1.f, 1.f)), make_float2(q0p, -q0p));
+      inc[1] = fma2(ns2, xa, zp[1]);
+      inc[2] = fma2(ns2, xb, zp[2]);
+      inc[3] = fma2(ns2, xc, zp[3]);
+      inc[4] = fma2(ns2, xd, zp[4]);
 #pragma unroll
-      for (int j = 1; j < K2 - 1; ++j) {
-        inc = fmaf(-s, xv[j], zp[j]);
-        socp = fmaf(inc, inc, socp);
-        a.betan[j * n0 + i] = ff_add_f(bt(tprev, j, xh, yh), ts * inc);
+      for (int k = 0; k < 5; ++k) socp = fma2(inc[k], inc[k], socp);
+      const int c0 = 0, c1 = K2 - 1;
+      ff2 B = ff2_add_f(ff2_pack(bt(tprev, c0, xh, yh), bt(tprev, c1, xh, yh)), mul2(ts2, inc[0]));
+      a.betan[c0 * n0 + i] = ff2_lane0(B);
+      a.betan[c1 * n0 + i] = ff2_lane1(B);
+#pragma unroll
+      for (int k = 1; k <= 4; ++k) {
+        const int j = 2 * k - 1;
+        B = ff2_add_f(ff2_pack(bt(tprev, j, xh, yh), bt(tprev, j + 1, xh, yh)), mul2(ts2, inc[k]));
+        a.betan[j * n0 + i] = ff2_lane0(B);
+        a.betan[(j + 1) * n0 + i] = ff2_lane1(B);
       }
-      inc = (zp[K2 - 1] - 1.f) - xv[0];
-      socp = fmaf(inc, inc, socp);
-      a.betan[(K2 - 1) * n0 + i] = ff_add_f(bt(tprev, K2 - 1, xh, yh), ts * inc);
     }
     // the next iteration's residual at the owned node of time t:
     // r = A^*(q - alpha/sigma) - c/sigma - A^*A phi = A^*(q - alpha/sigma - A phi) - c/sigma,
@@ -746,20 +821,22 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
     if (a.r && own_ok && write_node) {
       const int i = t * P + xo * N1 + yo;
       const int p = xo * N1 + yo;
-      float2 acc = make_float2(0.f, 0.f);
-      if (t >= 1) acc = ff_add(acc, ff_mul_f(w0p, ih0));
-      if (t < g.T) acc = ff_add(acc, ff_neg(ff_mul_f(w0c, ih0)));
+      ff_acc acc{0.f, 0.f};
+      if (t >= 1) acc_add_mul(acc, w0p, ih0);
+      if (t < g.T) acc_add_mul(acc, w0c, -ih0);
       // faces j = x - 1 / x (and y - 1 / y); the slots beyond the walls hold zero
-      acc = ff_add(acc, ff_mul_f(ff_add(sw1[lx * VY + ly], ff_neg(sw1[(lx + 1) * VY + ly])), ih1));
-      acc = ff_add(acc, ff_mul_f(ff_add(sw2[lx * (VY + 1) + ly], ff_neg(sw2[lx * (VY + 1) + ly + 1])), ih2));
-      if (t == 0) acc = ff_add(acc, ff_neg(ff_mul(a.c0[p], a.isg)));
-      if (t == g.T) acc = ff_add(acc, ff_mul(a.c1[p], a.isg));
-      a.r[i] = acc.x + acc.y;
+      acc_add_mul(acc, sw1[lx * VY + ly], ih1);
+      acc_add_mul(acc, sw1[(lx + 1) * VY + ly], -ih1);
+      acc_add_mul(acc, sw2[lx * (VY + 1) + ly], ih2);
+      acc_add_mul(acc, sw2[lx * (VY + 1) + ly + 1], -ih2);
+      if (t == 0) acc_add(acc, ff_neg(ff_mul(a.c0[p], a.isg)));
+      if (t == g.T) acc_add(acc, ff_mul(a.c1[p], a.isg));
+      a.r[i] = acc.h + acc.c;
     }
     q0p = q0c;
     w0p = w0c;
 #pragma unroll
-    for (int j = 0; j < K2; ++j) zp[j] = zc[j];
+    for (int k = 0; k < 5; ++k) zp[k] = zc[k];
     // no barrier here: step A of t+1 writes only ztn and ztp[lev of t+1] (read by
     // step B of t, which every thread finished before step C) and registers; step B
     // of t+1, which overwrites the faces step C reads, follows the barrier after A
@@ -775,7 +852,7 @@ __global__ void __launch_bounds__(kThreadsV2, kMinBlocksV2) k_fused2d_tma(const 
     return;
   }
   if (a.socp_part) {
-    double v = (double)socp;
+    double v = (double)socp.x + (double)socp.y;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __shared__ double wsum[kThreadsV2 / 32];
     if ((tid & 31) == 0) wsum[tid >> 5] = v;
