@@ -48,3 +48,23 @@ def oracle_solution(name, tol=1e-6, maxit=60000):
         res = O.solve(prob, st, tol=tol, maxit=maxit)
         _ORACLE_CACHE[key] = (spec, r0, r1, mask, g, prob, st, res)
     return _ORACLE_CACHE[key]
+
+
+_MIX_CACHE = {}
+
+
+def oracle_mixture(T, N, seed, masked=False, tol=1e-7, tau=1.9, maxit=400000):
+    """Oracle solve from zero of a seeded 2D Gaussian-mixture instance on an N^2 x T grid
+    (optionally with rectangle obstacles), cached for the test session.
+    Returns (r0, r1, mask, g, prob, st, res)."""
+    key = (T, N, seed, masked, tol, tau)
+    if key not in _MIX_CACHE:
+        from paper_2505_05424_gb300 import workloads as W
+        r0, r1, mask = W.mixture_pair(W.GridSpec(2, T, N), seed, obstacles=masked)
+        g = O.Grid(2, T, [N, N])
+        prob = O.Problem(g, r0, r1, mask)
+        st = O.State.zeros(g)
+        res = O.solve(prob, st, tol=tol, maxit=maxit, tau=tau)
+        assert res["eta_dot"] <= tol
+        _MIX_CACHE[key] = (r0, r1, mask, g, prob, st, res)
+    return _MIX_CACHE[key]

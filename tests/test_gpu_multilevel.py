@@ -1,10 +1,11 @@
 """The multilevel strategy (Sec. 5) on the GPU: coarse levels solved and
 interpolated onto the caller's grid, which then converges to the same solution
-as a cold start."""
+as a cold start and as the FP64 oracle solved from zero to eta_dot <= 1e-7."""
 import numpy as np
 import pytest
 
-from gpu_util import ensure_built
+import oracle as O
+from gpu_util import ensure_built, oracle_mixture
 from paper_2505_05424_gb300 import workloads as W
 from paper_2505_05424_gb300.solver import DotError, DotSolver
 
@@ -42,3 +43,27 @@ def test_multilevel_rejects_indivisible_grids():
     with pytest.raises(DotError):
         s.dot_solve_multilevel(2)       # 30 is not divisible by 4
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("masked", [False, True])
+def test_multilevel_matches_oracle(prec, masked):
+    """16^2 x 8 mixtures (seed 4100, with and without obstacles), two coarse levels
+    (8^2 x 4, 4^2 x 2), solved to eta_dot <= 1e-7 and compared with the oracle's cold
+    solve to the same tolerance: the objective within 1e-6 relative, the densities
+    within 1% of their maximum (measured differences are printed).  At 1e-6 the
+    objective itself still differs from its 1e-7 value by a few 1e-6 on this grid."""
+    tol = 1e-7
+    r0, r1, mask, g, prob, st, res = oracle_mixture(8, 16, 4100 + masked, masked=masked, tol=1e-7)
+    w_ref = O.w2_squared(g, res["primal_obj"])
+    rho_o = O.density_slices(g, st)
+    s = DotSolver(2, 8, 16, r0, r1, mask=mask, prec=prec)
+    rc, iters = s.dot_solve_multilevel(2, tol, 200000)
+    rho, m, phi, obj, kk = s.dot_get()
+    s.close()
+    d_rho = np.abs(rho - rho_o).max() / rho_o.max()
+    print(prec, masked, "levels (fine, 1/2, 1/4)", iters, "oracle", res["iterations"], "obj", obj, "ref", w_ref,
+          "rel", abs(obj - w_ref) / w_ref, "max|rho - rho_o| / max", d_rho)
+    assert rc == 0 and kk["eta_dot"] <= tol
+    assert abs(obj - w_ref) <= 1e-6 * w_ref
+    assert d_rho <= 1e-2

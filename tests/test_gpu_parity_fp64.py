@@ -169,3 +169,25 @@ def test_full_size_mix256_two_iterations():
     tol = fp64_tol(spec.T, [spec.N] * 2)
     assert rel_err(q2, st.q) < tol and rel_err(al2, st.alpha) < tol and rel_err(b2, st.beta) < tol
     gpu.close()
+
+
+@pytest.mark.parametrize("D,T,N", [(2, 3, [8, 1024]), (2, 5, [1024, 6])])
+def test_1024_axis(D, T, N):
+    """1024-long spatial axes (the scalability case's), first and last: the Poisson solve
+    and one iteration from a random state against the oracle."""
+    rng = np.random.default_rng(1100 + T)
+    g = O.Grid(D, T, N)
+    P = int(np.prod(N))
+    r0, r1 = rng.random(P) + 0.05, rng.random(P) + 0.05
+    _, prob, gpu = pair(D, T, N, r0, r1, prec="fp64", check_every=0)
+    tol = fp64_tol(T, N)
+    b = rng.standard_normal(g.n_nodes) + 0.5
+    assert rel_err(gpu.dot_poisson(b), O.poisson(g, b)) < tol
+    q, al, beta = random_state(g, rng)
+    st = O.State(g, np.zeros(g.n_nodes), np.zeros(g.K * g.n_cones), q.copy(), al.copy(), beta.copy(), 1.3)
+    O.iterate(prob, st, tau=1.9)
+    gpu.dot_set_state(q, al, beta, 1.3)
+    gpu.dot_solve(tol=0.0, maxit=1)
+    q2, al2, b2, _, _ = gpu.dot_get_state()
+    gpu.close()
+    assert rel_err(q2, st.q) < tol and rel_err(al2, st.alpha) < tol and rel_err(b2, st.beta) < tol

@@ -17,8 +17,8 @@ from paper_2505_05424_gb300.solver import DotError, DotServer, DotSolver
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-5
-MAXIT = 20000
+TOL = 1e-6          # the serving stream's tolerance
+MAXIT = 100000
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -88,7 +88,7 @@ def test_result_is_the_same_alone_and_in_the_mix():
         assert srv.wait(pid, 600.0) == 0
         mixed = srv.result(pid)
         for rid in ids:
-            assert srv.wait(rid, 600.0) in (0, 1)      # converged or maxit reached
+            assert srv.wait(rid, 600.0) == 0           # every request converged
         stats = srv.stats()
     assert stats["peak_running"] >= 2          # the probe shared the device with others
     same(alone, mixed)
