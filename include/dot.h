@@ -75,6 +75,15 @@ typedef struct {
                               a CUDA graph captured on first use; 0 = launch kernel by
                               kernel, as solves under dot_profile always do.  The
                               results are the same bit for bit; default 1 */
+  double tau_switch_below; /* mixed path: once a stopping-measure check finds eta_dot
+                              <= tau_switch_below, the dual step length becomes 1 (the
+                              tau of ALG2, Sec. 5.2) for the rest of the solve.  With
+                              tau near 2 the dual residual A^*alpha + c keeps a share
+                              (1 - tau) of itself each iteration and sums the FP32
+                              rounding of q and z (about 1e-7 relative) over ~1/(2 - tau)
+                              iterations, which stalls eta_dot near 2e-7; with tau = 1
+                              it does not.  0 = never; the FP64 path ignores it (it runs
+                              the oracle's fixed-tau recurrence); default 3e-7 */
 } dot_options;
 
 /* Index of each value in the kkt[] array filled by dot_get / dot_kkt. */

@@ -79,7 +79,8 @@ class DotGrid(ctypes.Structure):
 class DotOptions(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("tau", ctypes.c_double), ("sigma0", ctypes.c_double),
                 ("s_sigma", ctypes.c_double), ("s_r", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("obstacle_weight", ctypes.c_double), ("max_seconds", ctypes.c_double), ("use_graphs", ctypes.c_int)]
+                ("obstacle_weight", ctypes.c_double), ("max_seconds", ctypes.c_double), ("use_graphs", ctypes.c_int),
+                ("tau_switch_below", ctypes.c_double)]
 
 
 class DotServerOptions(ctypes.Structure):

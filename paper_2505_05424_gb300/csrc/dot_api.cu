@@ -144,6 +144,10 @@ int dot::check_options(const dot_options& o, std::string* why) {
     return DOT_EINVAL;
   }
   if (o.prec != DOT_FP64 && o.prec != DOT_MIXED) { *why = "unknown precision"; return DOT_EINVAL; }
+  if (!(o.tau_switch_below >= 0.0 && std::isfinite(o.tau_switch_below))) {
+    *why = "tau_switch_below must be >= 0";
+    return DOT_EINVAL;
+  }
   return DOT_OK;
 }
 
@@ -159,6 +163,7 @@ struct dot_ctx {
   double* h_red = nullptr;  // pinned R_NSLOTS doubles + one int (device error flag)
   std::vector<double> m0, m1, omega;
   double sigma = 1.0;
+  double tau_cur = 1.9;   // dual step length in use (opt.tau, or 1 after tau_switch_below)
   long iters = 0;
   double kkt[DOT_KKT_LEN];
   std::string err;
@@ -307,7 +312,7 @@ class PeriodGraphs {
     dot_ctx* c = c_;
     if (broken_ || c->prof || !c->opt.use_graphs || !c->path->graphable() || c->path->residual_carried())
       return kNoGraph;
-    c->path->set_penalty(c->sigma, c->opt.tau, c->stream, counter(c));
+    c->path->set_penalty(c->sigma, c->tau_cur, c->stream, counter(c));
     const int par = c->path->parity() & 1;
     if (!exec_[par] && !capture(par, ce)) {
       broken_ = true;
@@ -338,7 +343,7 @@ class PeriodGraphs {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      for (int it = 0; it < ce; ++it) c->path->iterate(c->sigma, c->opt.tau, c->cap, lc);
+      for (int it = 0; it < ce; ++it) c->path->iterate(c->sigma, c->tau_cur, c->cap, lc);
       c->path->kkt(c->cap, lc);
       cudaMemcpyAsync(c->h_red, c->path->red_out(), sizeof(double) * R_NSLOTS, cudaMemcpyDeviceToHost, c->cap);
       if (c->path->error_flag())
@@ -378,6 +383,7 @@ void dot_default_options(dot_options* o) {
   o->obstacle_weight = 1e-6;
   o->max_seconds = 0.0;
   o->use_graphs = 1;
+  o->tau_switch_below = 3e-7;
 }
 
 const char* dot_version(void) { return "dot-gb300 0.1 (sm_103a)"; }
@@ -442,6 +448,7 @@ int dot_create(const dot_grid* grid, const double* rho0, const double* rho1, con
     return fail(nullptr, rc, perr);
   }
   c->sigma = o.sigma0;
+  c->tau_cur = o.tau;
   c->iters = 0;
   for (int i = 0; i < DOT_KKT_LEN; ++i) c->kkt[i] = NAN;
   e = cudaStreamSynchronize(c->stream);
@@ -483,7 +490,7 @@ int dot_solve(dot_ctx* c, double tol, long maxit) {
         }
         prof_record(c, -1);
       }
-      c->path->iterate(c->sigma, c->opt.tau, c->stream, lc);
+      c->path->iterate(c->sigma, c->tau_cur, c->stream, lc);
       ++c->iters;
       ++k;
       if (ce > 0 && k % ce == 0) {
@@ -496,6 +503,9 @@ int dot_solve(dot_ctx* c, double tol, long maxit) {
       const double eta = c->kkt[DOT_KKT_ETA];
       if (!std::isfinite(eta)) return fail(c, DOT_EDIVERGED, "stopping measure is not finite");
       if (tol > 0.0 && eta <= tol) return DOT_OK;
+      // mixed path near its FP32 floor: the ALG2 step from now on
+      if (c->opt.prec == DOT_MIXED && c->opt.tau_switch_below > 0.0 && eta <= c->opt.tau_switch_below)
+        c->tau_cur = 1.0;
       // penalty rule (Sec. 5.3) on eta_P^soc / eta_D^soc
       const double ratio = c->kkt[DOT_KKT_ETA_P_SOC] / c->kkt[DOT_KKT_ETA_D_SOC];
       if (ratio > c->opt.s_r)
@@ -569,6 +579,7 @@ int dot_set_state(dot_ctx* c, const double* q, const double* alpha, const double
   if (rc != DOT_OK) return fail(c, rc, perr);
   c->sigma = sigma;
   c->iters = iters;
+  c->tau_cur = c->opt.tau;
   return DOT_OK;
 }
 

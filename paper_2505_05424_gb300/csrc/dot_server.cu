@@ -49,6 +49,7 @@ struct Request {
   int status = DOT_OK;
   long iters = 0;
   double sigma = 1.0;
+  double tau = 1.9;        // dual step length in use (as dot_solve: 1 after tau_switch_below)
   double kkt[DOT_KKT_LEN];
   double objective = NAN;
   std::vector<double> rho, m, phi;
@@ -231,7 +232,8 @@ bool dot_server::admit(Request* r) {
     k = 0;
   }
   std::string why;
-  if (target->mb->load_slot(k, r->m0, r->m1, r->has_mask ? &r->omega : nullptr, opt.sigma0, opt.tau,
+  r->tau = opt.tau;
+  if (target->mb->load_slot(k, r->m0, r->m1, r->has_mask ? &r->omega : nullptr, opt.sigma0, r->tau,
                             target->stream, &why) != DOT_OK) {
     fail_all("load_slot: " + why);
     return false;
@@ -349,13 +351,15 @@ void dot_server::finish_period(Batch& b) {
     if (!std::isfinite(eta)) { retire(b, k, DOT_EDIVERGED); continue; }
     if (r->tol > 0.0 && eta <= r->tol) { retire(b, k, DOT_OK); continue; }
     if (r->iters >= r->maxit) { retire(b, k, DOT_ENOTCONV); continue; }
+    // near the mixed path's FP32 floor: the ALG2 step from now on (as dot_solve)
+    if (opt.tau_switch_below > 0.0 && eta <= opt.tau_switch_below) r->tau = 1.0;
     // penalty rule (Sec. 5.3) on eta_P^soc / eta_D^soc
     const double ratio = r->kkt[DOT_KKT_ETA_P_SOC] / r->kkt[DOT_KKT_ETA_D_SOC];
     if (ratio > opt.s_r)
       r->sigma *= opt.s_sigma;
     else if (ratio < 1.0 / opt.s_r)
       r->sigma /= opt.s_sigma;
-    b.mb->set_sigma(k, r->sigma, opt.tau, true);
+    b.mb->set_sigma(k, r->sigma, r->tau, true);
   }
 }
 

@@ -78,6 +78,11 @@ def test_create_rejects_bad_arguments_before_any_device_call(lib):
     for name, value in rows:
         assert getattr(o, name) == float(value), name
     assert o.check_every == 10 and o.use_graphs == 1
+    # the mixed path's switch to the ALG2 step below its FP32 floor (Sec. 5.2's tau = 1)
+    assert o.tau_switch_below == 3e-7
+    o.tau_switch_below = -1.0
+    assert _create(lib, g, ok, ok, o)[0] == N.DOT_EINVAL and b"tau_switch_below" in lib.dot_last_error(None)
+    o.tau_switch_below = 3e-7
     o.tau = 2.0
     assert _create(lib, g, ok, ok, o)[0] == N.DOT_EINVAL
     o.tau = 1.9; o.s_r = 1.0
