@@ -75,14 +75,16 @@ __device__ __forceinline__ void proj_soc(int K, double* y) {
     return;
   }
   const double a = 0.5 * (y[0] + nb);
+  const double scale = a / nb;   // one division (FP64 divisions are costly on this GPU)
   y[0] = a;
-  for (int j = 1; j < K; ++j) y[j] = a * y[j] / nb;
+  for (int j = 1; j < K; ++j) y[j] = scale * y[j];
 }
 
 // Line 3: z = Pi_Q(B F q + d - beta/sigma), one cone per thread.
 __global__ void k_project(Geo g, F64Fields f, double sigma) {
   const long long n0 = (long long)g.T * g.P;
   const double s_default = sqrt(0.5);
+  const double isg = 1.0 / sigma;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
        i += (long long)gridDim.x * blockDim.x) {
     const long long p = i - (long long)plane_of(g, i) * g.P;
@@ -91,9 +93,9 @@ __global__ void k_project(Geo g, F64Fields f, double sigma) {
     const double s = f.somega ? f.somega[p] : s_default;
     const int K = g.K;
     double y[kMaxK];
-    y[0] = -x[0] + 1.0 - f.beta[i] / sigma;
-    for (int j = 1; j < K - 1; ++j) y[j] = s * x[j] - f.beta[(long long)j * n0 + i] / sigma;
-    y[K - 1] = x[0] + 1.0 - f.beta[(long long)(K - 1) * n0 + i] / sigma;
+    y[0] = -x[0] + 1.0 - f.beta[i] * isg;
+    for (int j = 1; j < K - 1; ++j) y[j] = s * x[j] - f.beta[(long long)j * n0 + i] * isg;
+    y[K - 1] = x[0] + 1.0 - f.beta[(long long)(K - 1) * n0 + i] * isg;
     proj_soc(K, y);
     for (int j = 0; j < K; ++j) f.z[(long long)j * n0 + i] = y[j];
   }
