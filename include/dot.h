@@ -169,7 +169,7 @@ int dot_poisson(dot_ctx *ctx, const double *b, double *phi);
  * replay), so that every kernel is bracketed.  dot_profile_read copies, for kernel ids
  * 0..max-1, the total milliseconds and launch counts; it returns the number of
  * kernel ids (DOT_NUM_KERNELS).  dot_kernel_name(id) names each id. */
-#define DOT_NUM_KERNELS 12
+#define DOT_NUM_KERNELS 13
 int dot_profile(dot_ctx *ctx, int enable);
 int dot_profile_read(dot_ctx *ctx, double *ms_total, long *launches, int max);
 const char *dot_kernel_name(int id);

@@ -204,7 +204,8 @@ namespace {
 
 const char* const kKernelNames[KID_COUNT] = {
     "assemble_b", "dct_axis", "dct_scale", "poisson_residual", "poisson_combine", "cone_project",
-    "update_q0_alpha0", "update_qd_alphad", "update_beta", "kkt_reductions", "dct_tcgen05", "fused_cone_update"};
+    "update_q0_alpha0", "update_qd_alphad", "update_beta", "kkt_reductions", "dct_tcgen05", "fused_cone_update",
+    "face_beta_residual"};
 
 // Record a CUDA event on the context's stream; kid < 0 marks a start point.
 void prof_record(dot_ctx* c, int kid) {

@@ -76,7 +76,7 @@ class MixedBatch {
   Geo g_;
   int G_;
   bool slot_masks_;
-  bool fused_ = false, tma_ = false;
+  bool fused_ = false, tma_ = false, fused3_ = false;
   int cur_ = 0;
   bool r_valid_ = false;   // f.r holds the next iteration's residual (from the fused kernel)
   std::unique_ptr<Buffers> B_;

@@ -164,7 +164,7 @@ struct DctTables64 {
 // Kernel ids for launch accounting and per-kernel timing (names in dot_api.cu).
 enum KernelId {
   KID_ASSEMBLE_B = 0, KID_DCT_AXIS, KID_SCALE, KID_RESIDUAL, KID_COMBINE, KID_PROJECT,
-  KID_UPDATE_Q0, KID_UPDATE_QD, KID_UPDATE_BETA, KID_KKT, KID_DCT_TC, KID_FUSED, KID_COUNT
+  KID_UPDATE_Q0, KID_UPDATE_QD, KID_UPDATE_BETA, KID_KKT, KID_DCT_TC, KID_FUSED, KID_FACE3, KID_COUNT
 };
 
 // Counts launches; when `mark` is set, it is called after every launch with the

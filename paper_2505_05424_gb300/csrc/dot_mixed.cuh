@@ -145,6 +145,13 @@ long long fused2d_tma_blocks(const Geo& g);
 // launch_solve_residual_mx).
 bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part, int* err,
                         bool residual, cudaStream_t s, LaunchCounter lc);
+// Fused lines 3-6 for D = 3 (k_fused3d.cu) for every active slot: z and q_0, alpha_0
+// by one pass over the cones, then q_d, alpha_d, beta by a time-marching pass over
+// tiles of cells; reads q, alpha, beta of f, writes those of fn; f.z is scratch.
+// residual: also write the next iteration's lines 1-2 residual into f.r.
+bool fused3d_supported(const Geo& g);
+void launch_fused3d(const Geo& g, int G, const MxFields& f, const MxFields& fn, bool residual, cudaStream_t s,
+                    LaunchCounter lc);
 // KKT partial-sum scratch (doubles) per slot.
 long long kkt_partials_len_mx(const Geo& g);
 

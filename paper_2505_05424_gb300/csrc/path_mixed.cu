@@ -50,7 +50,7 @@ void carve(const Geo& g, int G, bool masks, Carver& cv, MixedBatch::Buffers* B) 
   }
   B->f.beta = cv.take<float2>(Gs * g.K * n0);
   B->f2 = B->f;
-  if (fused2d_supported(g)) {
+  if (fused2d_supported(g) || fused3d_supported(g)) {   // q, alpha, beta double-buffered
     B->f2.q[0] = cv.take<float>(Gs * n0);
     B->f2.al[0] = cv.take<float2>(Gs * n0);
     for (int d = 0; d < g.D; ++d) {
@@ -58,6 +58,8 @@ void carve(const Geo& g, int G, bool masks, Carver& cv, MixedBatch::Buffers* B) 
       B->f2.al[1 + d] = cv.take<float2>(Gs * nn);
     }
     B->f2.beta = cv.take<float2>(Gs * g.K * n0);
+  }
+  if (fused2d_supported(g)) {
     B->f.z = nullptr;                       // z never leaves the fused kernel
     B->socp = cv.take<double>(Gs * socp_blocks(g));
   } else {
@@ -161,6 +163,7 @@ int MixedBatch::init(char* ws, size_t bytes, cudaStream_t s, std::string* err) {
   Buffers& B = *B_;
   fused_ = fused2d_supported(g_);
   tma_ = fused_ && fused2d_tma_supported(g_);
+  fused3_ = fused3d_supported(g_);
   if (G_ > 1 && !batchable(g_)) {
     *err = "this grid cannot be batched (needs D = 2 and every axis on the tensor cores)";
     return DOT_EINVAL;
@@ -174,7 +177,7 @@ int MixedBatch::init(char* ws, size_t bytes, cudaStream_t s, std::string* err) {
   f2.r = B.f.r;
   f2.bsum = B.f.bsum;
   f2.blo = B.f.blo;
-  if (!fused_) {
+  if (!fused_ && !fused3_) {
     for (int d = 0; d <= kMaxD; ++d) { f2.q[d] = B.f.q[d]; f2.al[d] = B.f.al[d]; }
     f2.beta = B.f.beta;
   }
@@ -261,7 +264,7 @@ cudaError_t MixedBatch::zero_slot(int b, cudaStream_t s) {
   Buffers& B = *B_;
   cudaError_t e = cudaMemsetAsync(B.f.phi + b * nn, 0, nn * 8, s);
   const MxFields* sets[2] = {&B.f, &B.f2};
-  for (int k = 0; k < (fused_ ? 2 : 1); ++k) {
+  for (int k = 0; k < (fused_ || fused3_ ? 2 : 1); ++k) {
     const MxFields& f = *sets[k];
     if (e == cudaSuccess) e = cudaMemsetAsync(f.q[0] + b * n0, 0, n0 * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(f.al[0] + b * n0, 0, n0 * 8, s);
@@ -367,6 +370,15 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
     // lines 3-6 (the TMA kernel also leaves the next residual in f.r)
     r_valid_ = tma_ && launch_fused2d_tma(g_, G_, fc, fn, B_->socp, B_->err, true, s, lc);
     if (!r_valid_) launch_fused2d(g_, G_, fc, fn, B_->socp, s, lc);
+    cur_ ^= 1;
+  } else if (fused3_) {
+    const MxFields& fc = cur();
+    const MxFields& fn = other();
+    if (r_valid_) launch_solve_residual_mx(g_, G_, fc, ps_, s, lc);
+    else launch_assemble_solve_mx(g_, G_, fc, ps_, s, lc);
+    // lines 3-6, and the next iteration's residual in f.r
+    launch_fused3d(g_, G_, fc, fn, true, s, lc);
+    r_valid_ = true;
     cur_ ^= 1;
   } else {
     launch_iterate_mx(g_, G_, B_->f, ps_, s, lc);

@@ -159,11 +159,18 @@ def test_gauss32_mixed_converges_to_fp64_objective():
     gpu.close()
 
 
-def test_mixed_lockstep_tracks_fp64():
-    """Tens of iterations: the mixed iterate stays within the FP32 noise of the oracle's."""
-    rng = np.random.default_rng(700)
-    r0, r1 = rng.random(120) + 0.05, rng.random(120) + 0.05
-    g, prob, gpu = pair(2, 8, [12, 10], r0, r1, prec="mixed", check_every=10)
+# 3D grids: several 4 x 4 x 32 tiles of the D = 3 face pass with ragged edges on
+# every axis, and more than one 16-node time chunk
+@pytest.mark.parametrize("D,T,N,masked", [(2, 8, [12, 10], False), (3, 20, [5, 6, 37], False),
+                                          (3, 4, [7, 4, 33], True)])
+def test_mixed_lockstep_tracks_fp64(D, T, N, masked):
+    """Tens of iterations: the mixed iterate stays within the FP32 noise of the oracle's
+    (every iteration after the first starts from the residual the previous one left)."""
+    rng = np.random.default_rng(700 if D == 2 else 710 + T)
+    P = int(np.prod(N))
+    r0, r1 = rng.random(P) + 0.05, rng.random(P) + 0.05
+    mask = (rng.random(P) < 0.2) if masked else None
+    g, prob, gpu = pair(D, T, N, r0, r1, mask=mask, prec="mixed", check_every=10)
     st = O.State.zeros(g)
     O.solve(prob, st, tol=0.0, maxit=50, check_every=10)
     gpu.dot_solve(tol=0.0, maxit=50)
