@@ -38,7 +38,7 @@ constexpr int NF3 = NFX + NFY + NFZ;       // 1808
 constexpr int kCells3 = FX * FY * FZ;      // 512
 constexpr int kThreads3 = 256;             // two cells per thread
 static_assert(kCells3 == 2 * kThreads3 && FZ == 32 && FY == 4, "cell and face numbering below");
-constexpr int kTchunk3 = 16;               // time nodes written per CTA
+constexpr int kTchunk3 = 8;                // time nodes written per CTA (more CTAs than SMs x 5 on 64^3 x 32)
 constexpr int kConeThreads = 256;
 constexpr float kSdef = 0.70710678118654752f;   // sqrt(omega/2) for omega = 1
 
@@ -196,7 +196,7 @@ __device__ __forceinline__ float2 w_time(const Fused3Args& a, int ic, int P) {
   return ff_add_f(ff_neg(a.aln[0][ic]), -gm);
 }
 
-__global__ void __launch_bounds__(kThreads3, 3) k_face3(Geo g, Fused3Args a_in) {
+__global__ void __launch_bounds__(kThreads3, 5) k_face3(Geo g, Fused3Args a_in) {
   const int slot = blockIdx.z / a_in.nchunk, chunk = blockIdx.z - slot * a_in.nchunk;
   if (!a_in.sp[slot].active) return;
   const Fused3Args a = slot3(a_in, g, slot);
