@@ -71,6 +71,8 @@ def parse():
                          "{32^2x16, 64^2x32, 128^2x32, 256^2x64}, Poisson arrivals, 20%% masked) through "
                          "the continuous-batching server and print its JSON line instead")
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the serving stream")
+    ap.add_argument("--serve-maxit", type=int, default=300000,
+                    help="iteration limit of each served request (obstacle instances need ~1e5 at tol 1e-6)")
     ap.add_argument("--multilevel", type=int, default=0,
                     help="solve every timed instance with the multilevel strategy over this many coarse levels")
     ap.add_argument("--coarse-tol", type=float, default=0.0,
@@ -183,7 +185,14 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
         # lines 3-6 fused: read q, alpha/sigma, beta/sigma (iteration k) and phi; write
         # q, alpha/sigma, beta/sigma (k+1) and the next iteration's residual r (FP32)
         "fused_cone_update": 2 * (w + ws) * nq + 2 * ws * K * n0 + wf * nc + w * nc,
+        # D = 3 face pass: read alpha_d/sigma, phi, beta/sigma, z and the new q_0,
+        # alpha_0/sigma; write q_d, alpha_d/sigma, beta/sigma and the residual r
+        "face_beta_residual": 2 * (w + ws) * D * nf + wf * nc + w * K * n0 + 2 * ws * K * n0 + (w + ws) * n0
+                              + w * nc,
     }
+    if prec != "fp64" and D == 3:
+        # D = 3 cone pass: read q, beta/sigma, phi, alpha_0/sigma; write z, q_0, alpha_0/sigma
+        table["cone_project"] = w * nq + ws * K * n0 + wf * nc + w * K * n0 + w * n0 + 2 * ws * n0
     return float(table.get(name, 0.0))
 
 
@@ -191,7 +200,7 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
 # the named workload, with the SHA-256 prefix of the kernel source it was taken on:
 # the figure is reported only while that source is unchanged (else traffic = null).
 NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"):
-               (597.195264e6 + 475.236096e6, "k_fused2d.cu", "2e517d2654914088")}
+               (603.142400e6 + 471.448320e6, "k_fused2d.cu", "359154644071fada")}
 
 
 def stored_traffic(kernel: str, workload: str, prec: str):
@@ -525,7 +534,7 @@ def run_serve(args):
         dt = ta - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        ids.append(srv.submit(2, T, N, r0, r1, mask=mask, tol=args.tol, maxit=args.maxit, keep_fields=False))
+        ids.append(srv.submit(2, T, N, r0, r1, mask=mask, tol=args.tol, maxit=args.serve_maxit, keep_fields=False))
     status = [srv.wait(i) for i in ids]
     wall = time.perf_counter() - t0
     clk = clocks.stop()
@@ -552,7 +561,9 @@ def run_serve(args):
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"serving stream, first {len(ids)} requests, Poisson arrivals at {args.rate}/s, "
                                   "grids uniform over 32^2x16, 64^2x32, 128^2x32, 256^2x64, 20% with rectangle "
-                                  "obstacles, seeded mixtures (seed 50000+i)", "tol": args.tol},
+                                  "obstacles, seeded mixtures (seed 50000+i)", "tol": args.tol,
+                      "maxit": args.serve_maxit,
+                      "arrivals_span_s": round(reqs[-1][0], 3) if reqs else 0.0},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "queue_p50": float(np.percentile(qwait, 50)), "queue_p99": float(np.percentile(qwait, 99))},
            "converged": int(sum(1 for s_ in status if s_ == 0)), "requests": len(ids),

@@ -120,9 +120,6 @@ void launch_solve_residual_mx(const Geo& g, int G, const MxFields& f, const MxPo
 // (b never stored), one solve, phi += delta.
 void launch_assemble_solve_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
                               LaunchCounter lc);
-// Lines 1-6 of Algorithm 2 for every active slot (unfused kernels; penalties from f.sp).
-void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
-                       LaunchCounter lc);
 // Stopping-measure sums of every active slot into out[G][R_NSLOTS].  socp_part
 // (nullable): per-block sums of |z - BFq - d|^2 written by the fused kernel,
 // nsocp per slot; when given, they replace the z-based term.

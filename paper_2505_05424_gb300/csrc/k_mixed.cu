@@ -1,5 +1,7 @@
-// k_mixed.cu -- mixed-precision kernels of Algorithm 2 (lines 1, 3, 4, 5, 6),
-// the exact-residual step of the Poisson refinement, and the stopping measures.
+// k_mixed.cu -- mixed-precision kernels of Algorithm 2 around the fused passes
+// (k_fused2d.cu, k_fused3d.cu): line 1 (the b-assembly fused with the warm-start
+// residual), the exact-residual step of the Poisson refinement, the multiplier
+// rescale after a penalty change, and the stopping measures.
 //
 // Storage: q and z in FP32; the multipliers as alpha/sigma and beta/sigma and
 // the potential phi as two-float pairs (hi, lo); the Poisson scratch in FP32.
@@ -278,137 +280,6 @@ __device__ __forceinline__ void gather_Fq(const Geo& g, float* const* q, long lo
   }
 }
 
-// Line 3: z = Pi_Q(B F q + d - beta/sigma), formed and projected in two-float
-// arithmetic (ff_proj_soc); z is stored rounded to FP32 (its O(1) value loses
-// only 2^-24 relative).
-template <int D>
-__global__ void k_project(Geo g, MxFields fb) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const MxFields f = slot_view(fb, g, slot);
-  constexpr int K = 4 * D + 2;
-  const long long n0 = (long long)g.T * g.P;
-  const float s_default = 0.70710678118654752f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i - (long long)plane_of(g, i) * g.P;
-    float x[K - 1];
-    gather_Fq<D>(g, f.q, i, p, x);
-    const float s = f.somega ? f.somega[p] : s_default;
-    float2 y[K];
-    y[0] = ff_add(two_sum(-x[0], 1.f), ff_neg(f.beta[i]));
-#pragma unroll
-    for (int j = 1; j < K - 1; ++j) y[j] = ff_add(two_prod(s, x[j]), ff_neg(f.beta[(long long)j * n0 + i]));
-    y[K - 1] = ff_add(two_sum(x[0], 1.f), ff_neg(f.beta[(long long)(K - 1) * n0 + i]));
-    ff_proj_soc<K>(y);
-#pragma unroll
-    for (int j = 0; j < K; ++j) f.z[(long long)j * n0 + i] = ff_round(y[j]);
-  }
-}
-
-// Lines 4-5 on the time faces (diagonal 3, F^*B^*u = u_{K-1} - u_0), the
-// right-hand side in two-float arithmetic (alpha/sigma and beta/sigma cancel).
-template <int D>
-__global__ void k_update_q0(Geo g, MxFields fb) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const float ts = fb.sp[slot].tau;
-  const MxFields f = slot_view(fb, g, slot);
-  constexpr int K = 4 * D + 2;
-  const long long n0 = (long long)g.T * g.P;
-  const float ih0 = (float)g.invh[0];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float2 gp = grad_pair(f.phi, i, i + g.P, ih0);
-    const long long oK = (long long)(K - 1) * n0 + i;
-    // u_{K-1} - u_0 = (z_{K-1} - z_0) + (beta_{K-1} - beta_0)/sigma
-    const float2 db = ff_add(f.beta[oK], ff_neg(f.beta[i]));
-    float2 rhs = ff_add(gp, ff_add(f.al[0][i], db));
-    rhs = ff_add_f(rhs, f.z[oK] - f.z[i]);
-    const float qn = ff_round(ff_div_f(rhs, 3.f));
-    f.q[0][i] = qn;
-    f.al[0][i] = ff_add_f(f.al[0][i], ts * grad_minus(gp, qn));
-  }
-}
-
-// Lines 4-5 on the faces of axis d (see the FP64 kernel for the cone bookkeeping):
-// rhs = A phi + (alpha + sum_c s_c beta_c)/sigma + sum_c s_c z_c with the
-// multiplier sum in two-float arithmetic.
-template <int D>
-__global__ void k_update_qd(Geo g, MxFields fb, int d) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const float ts = fb.sp[slot].tau;
-  const MxFields f = slot_view(fb, g, slot);
-  const long long n = (long long)(g.T + 1) * g.P;
-  const long long n0 = (long long)g.T * g.P;
-  const float s_default = 0.70710678118654752f;
-  const long long s = g.sst[d];
-  float* qd = f.q[1 + d];
-  float2* ad = f.al[1 + d];
-  const float ih = (float)g.invh[1 + d];
-  const int cbase = 1 + 4 * d;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int t = plane_of(g, i);
-    const long long p = i - (long long)t * g.P;
-    const int j = coord(g, p, d);
-    if (j > g.N[d] - 2) continue;
-    const float2 gp = grad_pair(f.phi, i, i + s, ih);
-    const float s_r = f.somega ? f.somega[p + s] : s_default;
-    const float s_l = f.somega ? f.somega[p] : s_default;
-    float2 mb = ad[i];          // alpha + sum s_c beta_c
-    float zs = 0.f, dg = 0.f;   // sum s_c z_c, sum s_c^2
-    if (t <= g.T - 1) {
-      const long long o1 = (long long)(cbase + 0) * n0 + i + s;
-      const long long o2 = (long long)(cbase + 1) * n0 + i;
-      mb = ff_add(mb, ff_add(ff_mul_f(f.beta[o1], s_r), ff_mul_f(f.beta[o2], s_l)));
-      zs += s_r * f.z[o1] + s_l * f.z[o2];
-      dg += s_r * s_r + s_l * s_l;
-    }
-    if (t >= 1) {
-      const long long o3 = (long long)(cbase + 2) * n0 + i - g.P + s;
-      const long long o4 = (long long)(cbase + 3) * n0 + i - g.P;
-      mb = ff_add(mb, ff_add(ff_mul_f(f.beta[o3], s_r), ff_mul_f(f.beta[o4], s_l)));
-      zs += s_r * f.z[o3] + s_l * f.z[o4];
-      dg += s_r * s_r + s_l * s_l;
-    }
-    const float2 rhs = ff_add_f(ff_add(gp, mb), zs);
-    const float qn = ff_round(ff_div_f(rhs, 1.f + dg));
-    qd[i] = qn;
-    ad[i] = ff_add_f(ad[i], ts * grad_minus(gp, qn));
-  }
-}
-
-// Line 6: beta += tau sigma (z - B F q - d).
-template <int D>
-__global__ void __launch_bounds__(kThreads, 3) k_update_beta(Geo g, MxFields fb) {
-  const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
-  const float ts = fb.sp[slot].tau;
-  const MxFields f = slot_view(fb, g, slot);
-  constexpr int K = 4 * D + 2;
-  const long long n0 = (long long)g.T * g.P;
-  const float s_default = 0.70710678118654752f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n0;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i - (long long)plane_of(g, i) * g.P;
-    float x[K - 1];
-    gather_Fq<D>(g, f.q, i, p, x);
-    const float s = f.somega ? f.somega[p] : s_default;
-    // increments z - BFq - d, each rounded once relative to itself:
-    // (z_0 - 1) and (z_{K-1} - 1) are exact for z in [1/2, 2]; z_j - s x_j by one FMA
-    f.beta[i] = ff_add_f(f.beta[i], ts * ((f.z[i] - 1.f) + x[0]));
-#pragma unroll
-    for (int j = 1; j < K - 1; ++j) {
-      const long long o = (long long)j * n0 + i;
-      f.beta[o] = ff_add_f(f.beta[o], ts * fmaf(-s, x[j], f.z[o]));
-    }
-    const long long o = (long long)(K - 1) * n0 + i;
-    f.beta[o] = ff_add_f(f.beta[o], ts * ((f.z[o] - 1.f) - x[0]));
-  }
-}
-
 // ---- stopping measures: FP32 terms, per-thread FP32 sums, FP64 tree -----------
 
 constexpr int kKktBlocks = 608;
@@ -665,23 +536,6 @@ void assemble_solve_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson
 }
 
 template <int D>
-void launch_iter_tmpl(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
-                      LaunchCounter lc) {
-  const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
-  assemble_solve_tmpl<D>(g, G, f, ps, s, lc);                                      // lines 1-2
-  k_project<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                   // line 3
-  lc.launched(KID_PROJECT);
-  k_update_q0<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);                 // lines 4-5
-  lc.launched(KID_UPDATE_Q0);
-  for (int d = 0; d < D; ++d) {
-    k_update_qd<D><<<dim3(grid_for(nn), G), kThreads, 0, s>>>(g, f, d);
-    lc.launched(KID_UPDATE_QD);
-  }
-  k_update_beta<D><<<dim3(grid_for(n0), G), kThreads, 0, s>>>(g, f);               // line 6
-  lc.launched(KID_UPDATE_BETA);
-}
-
-template <int D>
 void launch_kkt_tmpl(const Geo& g, int G, const MxFields& f, double* partials, double* out,
                      const double* socp_part, int nsocp, cudaStream_t s, LaunchCounter lc) {
   const int kb = kkt_blocks(g);
@@ -691,12 +545,6 @@ void launch_kkt_tmpl(const Geo& g, int G, const MxFields& f, double* partials, d
 }
 
 }  // namespace
-
-void launch_iterate_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, cudaStream_t s,
-                       LaunchCounter lc) {
-  if (g.D == 2) launch_iter_tmpl<2>(g, G, f, ps, s, lc);
-  else launch_iter_tmpl<3>(g, G, f, ps, s, lc);
-}
 
 void launch_poisson_refined_mx(const Geo& g, int G, const MxFields& f, const MxPoisson& ps, float2* out,
                                bool have_bsum, cudaStream_t s, LaunchCounter lc) {

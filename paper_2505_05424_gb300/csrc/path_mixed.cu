@@ -380,8 +380,6 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
     launch_fused3d(g_, G_, fc, fn, true, s, lc);
     r_valid_ = true;
     cur_ ^= 1;
-  } else {
-    launch_iterate_mx(g_, G_, B_->f, ps_, s, lc);
   }
 }
 
