@@ -330,35 +330,4 @@ __device__ __forceinline__ void ff2_proj_soc10(ff2* P) {
   P[0] = ff2{make_float2(a.x, scale * P[0].h.y), make_float2(a.y, 0.f)};
 }
 
-// ---- lane-pair forms of the running sum and the division (two faces at once) ----
-// Each lane computes exactly what the scalar function of the same name computes.
-struct ff2_acc {
-  float2 h, c;
-};
-__device__ __forceinline__ ff2_acc acc2_init(ff2 a) { return ff2_acc{a.h, a.l}; }
-__device__ __forceinline__ void acc2_add(ff2_acc& s, ff2 b) {
-  const ff2 t = two_sum2(s.h, b.h);
-  s.h = t.h;
-  s.c = add2(s.c, add2(t.l, b.l));
-}
-__device__ __forceinline__ void acc2_add_f(ff2_acc& s, float2 b) {
-  const ff2 t = two_sum2(s.h, b);
-  s.h = t.h;
-  s.c = add2(s.c, t.l);
-}
-__device__ __forceinline__ void acc2_add_mul(ff2_acc& s, ff2 b, float2 x) {
-  const float2 p = mul2(b.h, x);
-  const float2 e = fma2(b.l, x, fma2(b.h, x, make_float2(-p.x, -p.y)));
-  const ff2 t = two_sum2(s.h, p);
-  s.h = t.h;
-  s.c = add2(s.c, add2(t.l, e));
-}
-__device__ __forceinline__ ff2 acc2_get(const ff2_acc& s) { return quick_two_sum2(s.h, s.c); }
-__device__ __forceinline__ ff2 ff2_div_f_r(ff2 a, float2 b, float2 r) {
-  const float2 q1 = mul2(a.h, r);
-  const ff2 p = two_prod2(q1, b);
-  const float2 rem = add2(sub2(sub2(a.h, p.h), p.l), a.l);
-  return quick_two_sum2(q1, mul2(rem, r));
-}
-
 }  // namespace dot
