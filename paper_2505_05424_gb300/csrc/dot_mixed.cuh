@@ -134,10 +134,10 @@ long long fused2d_blocks(const Geo& g);
 void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part,
                     cudaStream_t s, LaunchCounter lc);
 // The same pass with beta staged by TMA (needs N_y even); socp_part:
-// fused2d_tma_blocks(g) doubles per slot.  Returns false if the tensor map cannot
+// fused2d_tma_blocks(g, G) doubles per slot (the time chunking depends on the batch size).  Returns false if the tensor map cannot
 // be built.
 bool fused2d_tma_supported(const Geo& g);
-long long fused2d_tma_blocks(const Geo& g);
+long long fused2d_tma_blocks(const Geo& g, int G);
 // residual: also write the next iteration's lines 1-2 residual into f.r (see
 // launch_solve_residual_mx).
 bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& fn, double* socp_part, int* err,

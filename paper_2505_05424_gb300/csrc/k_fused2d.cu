@@ -424,7 +424,16 @@ void launch_fused2d(const Geo& g, int G, const MxFields& f, const MxFields& fn, 
 namespace dot {
 namespace {
 
-constexpr int VX = 8, VY = 32;               // owned tile: one cone per thread
+#ifndef FUSED_V2_VX
+#define FUSED_V2_VX 8
+#endif
+#ifndef FUSED_V2_THREADS
+#define FUSED_V2_THREADS 352
+#endif
+#ifndef FUSED_V2_TCHUNK
+#define FUSED_V2_TCHUNK 16
+#endif
+constexpr int VX = FUSED_V2_VX, VY = 32;     // owned tile: one cone per thread
 constexpr int VHX = VX + 2, VHY = VY + 2;    // cone halo 10 x 34
 constexpr int VNH = VHX * VHY;               // 340 cones
 constexpr int VBW = VY + 4;                  // beta tile columns: y in [y0-2, y0+34)
@@ -446,10 +455,11 @@ constexpr int kSmemV2 = kOffBar + 64;
 static_assert(kOffW1 % 16 == 0, "two-float face arrays are 16-byte aligned");
 // 11 warps: one thread per cone of the 10 x 34 halo rectangle (256 owned + 84
 // ring cones), so phase A takes one round; 552 faces take two
-constexpr int kThreadsV2 = 352;
+constexpr int kThreadsV2 = FUSED_V2_THREADS;
+static_assert(kThreadsV2 >= VX * VY + 2 * (VX + VY + 2) && kThreadsV2 % 32 == 0, "a thread per halo cone");
 constexpr int kMinBlocksV2 = FUSED_V2_MIN_BLOCKS;
-// cone times per CTA: each chunk recomputes one cone time before it (1/kTchunkV2 extra)
-constexpr int kTchunkV2 = 16;
+// most cone times per CTA (fused2d_tma_tchunk)
+constexpr int kTchunkV2 = FUSED_V2_TCHUNK;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -872,8 +882,19 @@ namespace dot {
 
 bool fused2d_tma_supported(const Geo& g) { return g.D == 2 && g.N[1] % 2 == 0; }
 
-long long fused2d_tma_blocks(const Geo& g) {
-  const int tchunk = g.T <= kTchunkV2 ? g.T : kTchunkV2;
+// Cone times per CTA for a batch of G solves of grid g: kTchunkV2, halved (down to 2)
+// while the launch would have fewer than 256 CTAs, so that small grids still occupy
+// the GPU (measured: 128^2 x 32 80 -> 60 us per launch with 8, 32^2 x 16 66 -> 19 us
+// with 2); each chunk recomputes one cone time before it (1/tchunk extra work).
+int fused2d_tma_tchunk(const Geo& g, int G) {
+  const long long tiles = (long long)((g.N[0] + VX - 1) / VX) * ((g.N[1] + VY - 1) / VY) * G;
+  int tc = g.T <= kTchunkV2 ? g.T : kTchunkV2;
+  while (tc > 2 && tiles * ((g.T + tc - 1) / tc) < 256) tc = (tc + 1) / 2;
+  return tc;
+}
+
+long long fused2d_tma_blocks(const Geo& g, int G) {
+  const int tchunk = fused2d_tma_tchunk(g, G);
   return (long long)((g.N[0] + VX - 1) / VX) * ((g.N[1] + VY - 1) / VY) * ((g.T + tchunk - 1) / tchunk);
 }
 
@@ -891,11 +912,11 @@ bool launch_fused2d_tma(const Geo& g, int G, const MxFields& f, const MxFields& 
   a.phi = f.phi;
   a.somega = f.somega;
   a.ts = 0.f;
-  a.tchunk = g.T <= kTchunkV2 ? g.T : kTchunkV2;
+  a.tchunk = fused2d_tma_tchunk(g, G);
   a.nchunk = (g.T + a.tchunk - 1) / a.tchunk;
   a.sp = f.sp;
   a.socp_part = socp_part;
-  a.socp_per_slot = fused2d_tma_blocks(g);
+  a.socp_per_slot = fused2d_tma_blocks(g, G);
   a.err = err;
   a.r = residual ? f.r : nullptr;
   a.c0 = f.c0;

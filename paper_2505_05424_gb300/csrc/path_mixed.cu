@@ -36,7 +36,8 @@ struct MixedBatch::Buffers {
 
 namespace {
 
-long long socp_blocks(const Geo& g) { return std::max(fused2d_blocks(g), fused2d_tma_blocks(g)); }
+// per-slot partial sums of |z - BFq - d|^2 written by either fused kernel for a batch of G
+long long socp_blocks(const Geo& g, int G) { return std::max(fused2d_blocks(g), fused2d_tma_blocks(g, G)); }
 
 void carve(const Geo& g, int G, bool masks, Carver& cv, MixedBatch::Buffers* B) {
   const size_t nn = (size_t)(g.T + 1) * g.P, n0 = (size_t)g.T * g.P, P = (size_t)g.P;
@@ -61,7 +62,7 @@ void carve(const Geo& g, int G, bool masks, Carver& cv, MixedBatch::Buffers* B) 
   }
   if (fused2d_supported(g)) {
     B->f.z = nullptr;                       // z never leaves the fused kernel
-    B->socp = cv.take<double>(Gs * socp_blocks(g));
+    B->socp = cv.take<double>(Gs * socp_blocks(g, G));
   } else {
     B->f.z = cv.take<float>(Gs * g.K * n0);
     B->socp = nullptr;
@@ -276,7 +277,7 @@ cudaError_t MixedBatch::zero_slot(int b, cudaStream_t s) {
   }
   if (e == cudaSuccess && B.f.z) e = cudaMemsetAsync(B.f.z + b * g_.K * n0, 0, (size_t)g_.K * n0 * 4, s);
   if (e == cudaSuccess && B.socp)
-    e = cudaMemsetAsync(B.socp + b * socp_blocks(g_), 0, (size_t)socp_blocks(g_) * sizeof(double), s);
+    e = cudaMemsetAsync(B.socp + b * socp_blocks(g_, G_), 0, (size_t)socp_blocks(g_, G_) * sizeof(double), s);
   return e;
 }
 
@@ -386,7 +387,7 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
 void MixedBatch::kkt(cudaStream_t s, LaunchCounter lc) {
   r_valid_ = false;   // sigma may change after a check: the next iteration assembles afresh
   launch_kkt_mx(g_, G_, cur(), B_->partials, B_->red, fused_ ? B_->socp : nullptr,
-                fused_ ? (int)socp_blocks(g_) : 0, s, lc);
+                fused_ ? (int)socp_blocks(g_, G_) : 0, s, lc);
 }
 
 namespace {
