@@ -46,9 +46,14 @@ __host__ __device__ inline MxFields slot_view(MxFields f, const Geo& g, int b) {
   const long long nn = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P, P = g.P;
   f.q[0] += b * n0;
   f.al[0] += b * n0;
-  for (int d = 0; d < g.D; ++d) {
-    f.q[1 + d] += b * nn;
-    f.al[1 + d] += b * nn;
+  // constant indices (the bound is the array size), so that a kernel's copy of the
+  // fields stays in registers instead of local memory
+#pragma unroll
+  for (int d = 0; d < kMaxD; ++d) {
+    if (d < g.D) {
+      f.q[1 + d] += b * nn;
+      f.al[1 + d] += b * nn;
+    }
   }
   f.beta += b * g.K * n0;
   if (f.z) f.z += b * g.K * n0;

@@ -163,16 +163,12 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
               const __grid_constant__ CUtensorMap tm_blo, PassArgs pa) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sx[kStages];
-  uint8_t* sxlo[kStages];
-  uint8_t* sbh[kStages];
-  uint8_t* sbl[kStages];
-  for (int s = 0; s < kStages; ++s) {
-    sx[s] = smem + s * stage_bytes(pa.Nout);
-    sxlo[s] = sx[s] + kXBytes;
-    sbh[s] = sxlo[s] + kXBytes;
-    sbl[s] = sbh[s] + pa.Nout * kChunkK * 4;
-  }
+  // stage s: X hi, X lo, B hi, B lo (addresses computed, not kept in an indexed array)
+  const int sbytes = stage_bytes(pa.Nout);
+  auto sx = [&](int s) { return smem + s * sbytes; };
+  auto sxlo = [&](int s) { return smem + s * sbytes + kXBytes; };
+  auto sbh = [&](int s) { return smem + s * sbytes + 2 * kXBytes; };
+  auto sbl = [&](int s) { return smem + s * sbytes + 2 * kXBytes + pa.Nout * kChunkK * 4; };
   uint64_t* bars = (uint64_t*)(smem + kStages * stage_bytes(pa.Nout));
   const uint32_t ncols = (uint32_t)tmem_cols(pa.Nout);
   uint64_t* full = bars;                 // TMA landed
@@ -228,10 +224,10 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
         if (c >= kStages && !mbar_wait(&empty[s], (it - 1) & 1)) { atomicExch(&s_fail, 1); break; }
         if (s_fail) break;
         mbar_expect_tx(&full[s], bytes);
-        if (pa.mode != TC_ROWS_A) tma_load_2d(sx[s], &tm_x, &full[s], c * kChunkK, (int)row0);
-        else tma_load_4d(sx[s], &tm_x, &full[s], c * kChunkK, bfix, a0, gfix);
-        tma_load_2d(sbh[s], &tm_bhi, &full[s], c * kChunkK, n0);
-        tma_load_2d(sbl[s], &tm_blo, &full[s], c * kChunkK, n0);
+        if (pa.mode != TC_ROWS_A) tma_load_2d(sx(s), &tm_x, &full[s], c * kChunkK, (int)row0);
+        else tma_load_4d(sx(s), &tm_x, &full[s], c * kChunkK, bfix, a0, gfix);
+        tma_load_2d(sbh(s), &tm_bhi, &full[s], c * kChunkK, n0);
+        tma_load_2d(sbl(s), &tm_blo, &full[s], c * kChunkK, n0);
       }
     }
   } else if (warp == 1) {
@@ -242,8 +238,8 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
         if (!mbar_wait(&conv[s], it & 1)) { atomicExch(&s_fail, 1); break; }
         if (s_fail) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t ax = smem_u32(sx[s]), al = smem_u32(sxlo[s]);
-        const uint32_t bh = smem_u32(sbh[s]), bl = smem_u32(sbl[s]);
+        const uint32_t ax = smem_u32(sx(s)), al = smem_u32(sxlo(s));
+        const uint32_t bh = smem_u32(sbh(s)), bl = smem_u32(sbl(s));
 #pragma unroll
         for (int kk = 0; kk < kChunkK / 8; ++kk) {
           const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K inside the swizzle atom
@@ -264,8 +260,8 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
       // warp-uniform decision: every lane waits, the warp leaves together
       const bool got = __all_sync(0xffffffffu, mbar_wait(&full[s], it & 1));
       if (!got) { atomicExch(&s_fail, 1); break; }
-      float4* px = reinterpret_cast<float4*>(sx[s]);
-      float4* pl = reinterpret_cast<float4*>(sxlo[s]);
+      float4* px = reinterpret_cast<float4*>(sx(s));
+      float4* pl = reinterpret_cast<float4*>(sxlo(s));
 #pragma unroll 4
       for (int e = t; e < kXBytes / 16; e += 128) {
         float4 v = px[e];
@@ -291,7 +287,7 @@ k_dct_pass_tc(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ 
       // KEEP: this warp's copy of the time eigenvalues lam_0(n0 .. n0 + nout) in
       // stage 0's X tile, which no TMA load or MMA touches once the accumulator is
       // complete (one copy per warp: no barrier across warps)
-      float* slam = reinterpret_cast<float*>(sx[0]) + (warp - 2) * kMaxN;
+      float* slam = reinterpret_cast<float*>(sx(0)) + (warp - 2) * kMaxN;
       if (pa.mode == TC_KEEP) {
         for (int i = lane; i < nout; i += 32) slam[i] = n0 + i < pa.K ? pa.lam[0][n0 + i] : 1.f;
         __syncwarp();

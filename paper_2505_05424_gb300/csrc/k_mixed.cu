@@ -282,7 +282,12 @@ __device__ __forceinline__ void gather_Fq(const Geo& g, float* const* q, long lo
 
 // ---- stopping measures: FP32 terms, per-thread FP32 sums, FP64 tree -----------
 
-constexpr int kKktBlocks = 608;
+#ifndef KKT_MIN_BLOCKS
+#define KKT_MIN_BLOCKS 3
+#endif
+// most blocks per slot of the stopping-measure kernel: one wave of KKT_MIN_BLOCKS
+// CTAs on each of the GPU's 152 SMs
+constexpr int kKktBlocks = 152 * KKT_MIN_BLOCKS;
 
 __host__ __device__ inline long long kkt_partials_len_slot(const Geo& g) {
   return (long long)(g.D + 2) * kKktBlocks * R_NSLOTS;
@@ -298,6 +303,7 @@ inline int kkt_blocks(const Geo& g) {
 __device__ __forceinline__ void block_reduce_store(const float* accf, const double* accd, double* out_row) {
   __shared__ double sh[kThreads / 32][R_NSLOTS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
   for (int k = 0; k < R_NSLOTS; ++k) {
     double v = (double)accf[k] + accd[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -434,9 +440,11 @@ __device__ __forceinline__ void kkt_node(const Geo& g, const MxFields& f, float2
   }
 }
 
-// All stopping-measure sums in one pass over the nodes (one partial row per block).
+// All stopping-measure sums (one partial row per block), in D + 2 passes over the
+// nodes: the cones, the faces of each axis, the nodes.  Separate loops keep each
+// pass's loads in flight with few registers (one fused loop body needed ~220).
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1) k_kkt(Geo g, MxFields fb, double* partials_all, int use_z) {
+__global__ void __launch_bounds__(kThreads, KKT_MIN_BLOCKS) k_kkt(Geo g, MxFields fb, double* partials_all, int use_z) {
   const int slot = blockIdx.y;
   if (!fb.sp[slot].active) return;
   const MxFields f = slot_view(fb, g, slot);
@@ -444,21 +452,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_kkt(Geo g, MxFields fb, double*
   const float sg = sg2.x + sg2.y;
   double* partials = partials_all + slot * kkt_partials_len_slot(g);
   float acc[R_NSLOTS];
+#pragma unroll
   for (int k = 0; k < R_NSLOTS; ++k) acc[k] = 0.f;
   double dres = 0.0, cphi = 0.0;
   float2 dual = make_float2(0.f, 0.f);
-  const long long n = (long long)(g.T + 1) * g.P;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long n = (long long)(g.T + 1) * g.P, n0 = (long long)g.T * g.P;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+#pragma unroll 1
+  for (long long i = i0; i < n0; i += stride) {
     const int t = plane_of(g, i);
-    const long long p = i - (long long)t * g.P;
-    if (t < g.T) kkt_cone<D>(g, f, sg, i, p, use_z, acc);
+    kkt_cone<D>(g, f, sg, i, i - (long long)t * g.P, use_z, acc);
+  }
 #pragma unroll
-    for (int d = 0; d < D; ++d)
+  for (int d = 0; d < D; ++d) {
+#pragma unroll 1
+    for (long long i = i0; i < n; i += stride) {
+      const int t = plane_of(g, i);
+      const long long p = i - (long long)t * g.P;
       if (coord(g, p, d) <= g.N[d] - 2) kkt_face<D>(g, f, sg, d, i, t, p, acc, &dual);
-    kkt_node<D>(g, f, sg2, i, t, p, acc, &dres, &cphi);
+    }
+  }
+#pragma unroll 1
+  for (long long i = i0; i < n; i += stride) {
+    const int t = plane_of(g, i);
+    kkt_node<D>(g, f, sg2, i, t, i - (long long)t * g.P, acc, &dres, &cphi);
   }
   double accd[R_NSLOTS];
+#pragma unroll
   for (int k = 0; k < R_NSLOTS; ++k) accd[k] = 0.0;
   accd[R_DUALRES] = dres;
   accd[R_CPHI] = cphi;
