@@ -71,6 +71,10 @@ def parse():
                          "{32^2x16, 64^2x32, 128^2x32, 256^2x64}, Poisson arrivals, 20%% masked) through "
                          "the continuous-batching server and print its JSON line instead")
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the serving stream")
+    ap.add_argument("--serve-multilevel", type=int, default=0,
+                    help="serve large requests with the multilevel warm start over this many coarse levels")
+    ap.add_argument("--serve-ml-min-nodes", type=int, default=500000,
+                    help="requests with at least this many nodes get the multilevel warm start")
     ap.add_argument("--serve-maxit", type=int, default=300000,
                     help="iteration limit of each served request (obstacle instances need ~1e5 at tol 1e-6)")
     ap.add_argument("--multilevel", type=int, default=0,
@@ -200,7 +204,7 @@ def algorithmic_bytes(name: str, D: int, T: int, N: int, prec: str) -> float:
 # the named workload, with the SHA-256 prefix of the kernel source it was taken on:
 # the figure is reported only while that source is unchanged (else traffic = null).
 NCU_TRAFFIC = {("fused_cone_update", "mix256", "mixed"):
-               (603.142400e6 + 471.448320e6, "k_fused2d.cu", "359154644071fada")}
+               (602.547968e6 + 470.987264e6, "k_fused2d.cu", "bb3e412ee73d11ba")}
 
 
 def stored_traffic(kernel: str, workload: str, prec: str):
@@ -526,7 +530,7 @@ def run_serve(args):
         for i in ids:
             srv.wait(i)
     clocks = ClockSampler(0)
-    srv = DotServer()
+    srv = DotServer(multilevel=args.serve_multilevel, multilevel_min_nodes=args.serve_ml_min_nodes)
     clocks.start()
     t0 = time.perf_counter()
     ids = []
@@ -562,7 +566,8 @@ def run_serve(args):
            "config": {"workload": f"serving stream, first {len(ids)} requests, Poisson arrivals at {args.rate}/s, "
                                   "grids uniform over 32^2x16, 64^2x32, 128^2x32, 256^2x64, 20% with rectangle "
                                   "obstacles, seeded mixtures (seed 50000+i)", "tol": args.tol,
-                      "maxit": args.serve_maxit,
+                      "maxit": args.serve_maxit, "multilevel": args.serve_multilevel,
+                      "multilevel_min_nodes": args.serve_ml_min_nodes,
                       "arrivals_span_s": round(reqs[-1][0], 3) if reqs else 0.0},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "queue_p50": float(np.percentile(qwait, 50)), "queue_p99": float(np.percentile(qwait, 99))},

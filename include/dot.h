@@ -260,6 +260,12 @@ typedef struct {
                           within [1, max_slots] slots (default 4,194,304) */
   int use_graphs;      /* 1: one captured CUDA graph per batch and period (default); 0: plain launches */
   int idle_ms;         /* a batch with no solve for this long returns its memory (default 200) */
+  int multilevel;      /* > 0: warm-start each large request by the multilevel strategy of Sec. 5 over
+                          this many coarse levels, every level served as a request of its own grid
+                          (as dot_solve_multilevel); 0 = off (default) */
+  long long multilevel_min_nodes;  /* only requests with at least this many nodes (T+1) N_1..N_D and a
+                                      grid divisible by 2^multilevel (default 1,000,000) */
+  double multilevel_coarse_tol;    /* tolerance of the coarse levels; 0 = max(tol 10^-v, 1e-6) */
 } dot_server_options;
 
 void dot_server_default_options(dot_server_options *o);

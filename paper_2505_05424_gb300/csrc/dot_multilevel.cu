@@ -208,12 +208,10 @@ const char* dot_multilevel_last_error(void) { return g_ml_err.c_str(); }
 
 }  // extern "C"
 
-namespace {
-
 // Densities (any positive scale) averaged over 2 x ... x 2 blocks of cells, and
 // the mask of blocks that contain a masked cell.
-void coarsen(const dot_grid& gf, const std::vector<double>& rf, const std::vector<uint8_t>* mf, dot_grid* gc,
-             std::vector<double>* rc, std::vector<uint8_t>* mc) {
+void dot::coarsen(const dot_grid& gf, const std::vector<double>& rf, const std::vector<uint8_t>* mf, dot_grid* gc,
+                  std::vector<double>* rc, std::vector<uint8_t>* mc) {
   *gc = gf;
   gc->T = gf.T / 2;
   for (int d = 0; d < gf.D; ++d) gc->N[d] = gf.N[d] / 2;
@@ -240,7 +238,24 @@ void coarsen(const dot_grid& gf, const std::vector<double>& rf, const std::vecto
   }
 }
 
-}  // namespace
+
+bool dot::multilevel_ok(const dot_grid& g, int levels, std::string* why) {
+  const int f = 1 << levels;
+  if (g.T % f != 0 || g.T / f < 1) {
+    *why = "T must be divisible by 2^levels";
+    return false;
+  }
+  for (int d = 0; d < g.D; ++d)
+    if (g.N[d] % f != 0 || g.N[d] / f < 2) {
+      *why = "every N_d must be divisible by 2^levels with at least 2 coarse cells";
+      return false;
+    }
+  return true;
+}
+
+double dot::level_tol(double tol, double coarse_tol, int v) {
+  return coarse_tol > 0.0 ? coarse_tol : std::max(tol * std::pow(10.0, -v), 1e-6);
+}
 
 extern "C" int dot_solve_multilevel(dot_ctx* ctx, int levels, double tol, double coarse_tol, long maxit,
                                     long* iters) {
@@ -263,16 +278,7 @@ extern "C" int dot_solve_multilevel(dot_ctx* ctx, int levels, double tol, double
     g_ml_err = "levels must lie in [0, 8]";
     return DOT_EINVAL;
   }
-  const int f = 1 << levels;
-  if (g.T % f != 0 || g.T / f < 1) {
-    g_ml_err = "T must be divisible by 2^levels";
-    return DOT_EINVAL;
-  }
-  for (int d = 0; d < g.D; ++d)
-    if (g.N[d] % f != 0 || g.N[d] / f < 2) {
-      g_ml_err = "every N_d must be divisible by 2^levels with at least 2 coarse cells";
-      return DOT_EINVAL;
-    }
+  if (!multilevel_ok(g, levels, &g_ml_err)) return DOT_EINVAL;
   // the pyramid of densities, finest first
   std::vector<dot_grid> grids(levels + 1);
   std::vector<std::vector<double>> R0(levels + 1), R1(levels + 1);
@@ -320,7 +326,7 @@ extern "C" int dot_solve_multilevel(dot_ctx* ctx, int levels, double tol, double
     }
     // per-level tolerance: coarse_tol when given, else the paper's max(tol * 10^-v,
     // 1e-6); the caller's grid tol
-    const double tv = v == 0 ? tol : coarse_tol > 0.0 ? coarse_tol : std::max(tol * std::pow(10.0, -v), 1e-6);
+    const double tv = v == 0 ? tol : level_tol(tol, coarse_tol, v);
     int rc = dot_solve(c, tv, maxit);
     if (iters) {
       long it = 0;

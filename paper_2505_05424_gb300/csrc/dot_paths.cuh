@@ -43,6 +43,14 @@ class DeviceScope {
   int prev_ = 0;
   bool set_ = false;
 };
+// The multilevel strategy of Sec. 5 (dot_multilevel.cu): densities averaged over
+// 2 x ... x 2 blocks (a block is an obstacle if any of its cells is); whether a grid
+// can be coarsened `levels` times; level v's tolerance (coarse_tol when given, else
+// the paper's max(tol 10^-v, 1e-6)).
+void coarsen(const dot_grid& gf, const std::vector<double>& rf, const std::vector<uint8_t>* mf, dot_grid* gc,
+             std::vector<double>* rc, std::vector<uint8_t>* mc);
+bool multilevel_ok(const dot_grid& g, int levels, std::string* why);
+double level_tol(double tol, double coarse_tol, int v);
 // Stopping measures of Sec. 5.3 (kkt[DOT_KKT_LEN]) from the reduction slots r;
 // cn2 = sum of squares of c.
 void kkt_measures(const Geo& g, double cn2, const double* r, long iters, double sigma, double* kkt);

@@ -54,6 +54,18 @@ struct Request {
   double objective = NAN;
   std::vector<double> rho, m, phi;
   double t_submit = 0, t_admit = 0, t_done = 0;
+  // multilevel warm start (Sec. 5): the grids and the caller's densities coarsest
+  // first, the request's own grid last; lv = the level in progress.  Each level is
+  // served like a request of its grid; a finished coarse level's state, prolonged,
+  // starts the next one (as dot_solve_multilevel does with contexts).
+  std::vector<dot_grid> ml_grid;
+  std::vector<std::vector<double>> ml_r0, ml_r1;
+  std::vector<std::vector<uint8_t>> ml_mask;
+  int lv = 0;
+  double tol_final = 1e-6;
+  std::vector<double> init_q, init_al, init_beta;   // prolonged state for the next admission
+  double init_sigma = 0.0;
+  long coarse_iters = 0;
 };
 
 struct Batch {
@@ -124,11 +136,47 @@ struct dot_server {
   void retire(Batch& b, int k, int status);
   void free_batch(Batch& b);
   void fail_all(const std::string& why);
+  bool next_level(Batch& b, int k);
 };
 
 namespace {
 
 thread_local std::string g_srv_err;
+
+// Make level lv of request r's multilevel strategy the one it is served at: its
+// grid, its densities (prepared as dot_create prepares them) and its tolerance.
+int set_level(Request* r, int lv, const dot_options& opt, double coarse_tol, std::string* why) {
+  const int L = (int)r->ml_grid.size() - 1;
+  r->lv = lv;
+  r->grid = r->ml_grid[lv];
+  r->geo = make_geo(r->grid);
+  const bool masked = !r->ml_mask[lv].empty();
+  r->m0.clear();
+  r->m1.clear();
+  r->omega.clear();
+  const int rc = prepare_densities(r->geo, r->ml_r0[lv].data(), r->ml_r1[lv].data(),
+                                   masked ? r->ml_mask[lv].data() : nullptr, opt.obstacle_weight, &r->m0, &r->m1,
+                                   &r->omega, &r->has_mask, why);
+  r->cn2 = 0.0;
+  for (double v : r->m0) r->cn2 += v * v;
+  for (double v : r->m1) r->cn2 += v * v;
+  r->tol = lv == L ? r->tol_final : level_tol(r->tol_final, coarse_tol, L - lv);
+  return rc;
+}
+
+// Elements of q (and alpha) and of beta in the natural layouts of the C ABI.
+long long state_q_len(const dot_grid& g) {
+  long long P = 1;
+  for (int d = 0; d < g.D; ++d) P *= g.N[d];
+  long long n = (long long)g.T * P;
+  for (int d = 0; d < g.D; ++d) n += (long long)(g.T + 1) * (P / g.N[d]) * (g.N[d] - 1);
+  return n;
+}
+long long state_beta_len(const dot_grid& g) {
+  long long P = 1;
+  for (int d = 0; d < g.D; ++d) P *= g.N[d];
+  return (long long)(4 * g.D + 2) * g.T * P;
+}
 
 int sfail(dot_server* s, int code, const std::string& m) {
   if (s) {
@@ -238,12 +286,24 @@ bool dot_server::admit(Request* r) {
     fail_all("load_slot: " + why);
     return false;
   }
+  r->sigma = opt.sigma0;
+  if (!r->init_q.empty()) {
+    // a finer level of the multilevel strategy: start from the prolonged state
+    if (target->mb->write_state(k, r->init_q.data(), r->init_al.data(), r->init_beta.data(), r->init_sigma, r->tau,
+                                target->stream, &why) != DOT_OK) {
+      fail_all("write_state: " + why);
+      return false;
+    }
+    r->sigma = r->init_sigma;
+    r->init_q = std::vector<double>();
+    r->init_al = std::vector<double>();
+    r->init_beta = std::vector<double>();
+  }
   target->slot[k] = r;
   r->iters = 0;
-  r->sigma = opt.sigma0;
   std::lock_guard<std::mutex> l(mu);
   r->state = Q_RUNNING;
-  r->t_admit = now();
+  if (r->t_admit == 0.0) r->t_admit = now();
   return true;
 }
 
@@ -297,8 +357,36 @@ void dot_server::launch_period(Batch& b) {
   kernel_launches += (double)launches;
 }
 
+// A coarse level of slot k's request has finished: its state, prolonged to the next
+// finer grid, starts that level, for which the request is queued again.
+bool dot_server::next_level(Batch& b, int k) {
+  Request* r = b.slot[k];
+  const dot_grid gc = r->ml_grid[r->lv], gf = r->ml_grid[r->lv + 1];
+  std::vector<double> q(state_q_len(gc)), al(state_q_len(gc)), beta(state_beta_len(gc));
+  std::string why;
+  if (b.mb->read_state(k, q.data(), al.data(), beta.data(), b.stream, &why) != DOT_OK) return false;
+  r->init_q.assign(state_q_len(gf), 0.0);
+  r->init_al.assign(state_q_len(gf), 0.0);
+  r->init_beta.assign(state_beta_len(gf), 0.0);
+  if (dot_prolong_state(&gc, &gf, q.data(), al.data(), beta.data(), r->init_q.data(), r->init_al.data(),
+                        r->init_beta.data()) != DOT_OK)
+    return false;
+  r->init_sigma = r->sigma;
+  r->coarse_iters += r->iters;
+  if (set_level(r, r->lv + 1, opt, sopt.multilevel_coarse_tol, &why) != DOT_OK) return false;
+  b.mb->set_active(k, false);
+  b.slot[k] = nullptr;
+  if (b.active() == 0) b.idle_since = Clock::now();
+  queued.push_front(r);   // ahead of later arrivals: it has waited already
+  return true;
+}
+
 void dot_server::retire(Batch& b, int k, int status) {
   Request* r = b.slot[k];
+  if (status >= 0 && r->lv + 1 < (int)r->ml_grid.size()) {
+    if (next_level(b, k)) return;
+    status = DOT_ECUDA;
+  }
   if (status >= 0 && r->keep) {
     const Geo& g = b.geo;
     const long long n0 = (long long)g.T * g.P, nn = (long long)(g.T + 1) * g.P;
@@ -453,6 +541,9 @@ void dot_server_default_options(dot_server_options* o) {
   o->target_nodes = 4194304;
   o->use_graphs = 1;
   o->idle_ms = 200;
+  o->multilevel = 0;
+  o->multilevel_min_nodes = 1000000;
+  o->multilevel_coarse_tol = 0.0;
 }
 
 int dot_server_create(const dot_options* opt, const dot_server_options* sopt, dot_server** out) {
@@ -469,6 +560,8 @@ int dot_server_create(const dot_options* opt, const dot_server_options* sopt, do
   if (sopt) so = *sopt;
   if (so.max_slots < 1 || so.max_slots > 256) return sfail(nullptr, DOT_EINVAL, "max_slots must lie in [1, 256]");
   if (so.target_nodes < 1) return sfail(nullptr, DOT_EINVAL, "target_nodes must be >= 1");
+  if (so.multilevel < 0 || so.multilevel > 8) return sfail(nullptr, DOT_EINVAL, "multilevel must lie in [0, 8]");
+  if (!(so.multilevel_coarse_tol >= 0.0)) return sfail(nullptr, DOT_EINVAL, "multilevel_coarse_tol must be >= 0");
   std::unique_ptr<dot_server> s(new dot_server());
   s->opt = o;
   if (cudaGetDevice(&s->device) != cudaSuccess) return sfail(nullptr, DOT_ECUDA, "no CUDA device");
@@ -510,6 +603,43 @@ int dot_server_submit(dot_server* s, const dot_grid* grid, const double* rho0, c
   r->tol = tol;
   r->maxit = maxit;
   r->keep = keep_fields != 0;
+  const int L = s->sopt.multilevel;
+  std::string mwhy;
+  if (L > 0 && nodes_of(*grid) >= s->sopt.multilevel_min_nodes && multilevel_ok(*grid, L, &mwhy)) {
+    // the pyramid of the multilevel strategy, served coarsest first: the prepared
+    // densities and the obstacle cells (weight != 1) averaged as dot_solve_multilevel
+    // averages a context's
+    std::vector<dot_grid> gs(L + 1);
+    std::vector<std::vector<double>> R0(L + 1), R1(L + 1);
+    std::vector<std::vector<uint8_t>> M(L + 1);
+    const bool masked = r->has_mask;
+    gs[0] = *grid;
+    R0[0] = r->m0;
+    R1[0] = r->m1;
+    if (masked) {
+      M[0].assign(r->omega.size(), 0);
+      for (size_t i = 0; i < r->omega.size(); ++i) M[0][i] = r->omega[i] != 1.0;
+    }
+    for (int v = 1; v <= L; ++v) {
+      coarsen(gs[v - 1], R0[v - 1], masked ? &M[v - 1] : nullptr, &gs[v], &R0[v], &M[v]);
+      dot_grid gtmp;
+      std::vector<uint8_t> mtmp;
+      coarsen(gs[v - 1], R1[v - 1], nullptr, &gtmp, &R1[v], &mtmp);
+    }
+    // the caller's own grid keeps the caller's densities, prepared as at submission
+    const long long P = r->geo.P;
+    R0[0].assign(rho0, rho0 + P);
+    R1[0].assign(rho1, rho1 + P);
+    M[0] = mask ? std::vector<uint8_t>(mask, mask + P) : std::vector<uint8_t>();
+    for (int v = L; v >= 0; --v) {
+      r->ml_grid.push_back(gs[v]);
+      r->ml_r0.push_back(std::move(R0[v]));
+      r->ml_r1.push_back(std::move(R1[v]));
+      r->ml_mask.push_back(v == 0 || masked ? std::move(M[v]) : std::vector<uint8_t>());
+    }
+    r->tol_final = tol;
+    if (set_level(r.get(), 0, s->opt, s->sopt.multilevel_coarse_tol, &why) != DOT_OK) return sfail(s, DOT_EINVAL, why);
+  }
   for (int i = 0; i < DOT_KKT_LEN; ++i) r->kkt[i] = NAN;
   std::lock_guard<std::mutex> l(s->mu);
   if (!s->fatal.empty()) {

@@ -228,3 +228,38 @@ def test_1024_plane_one_iteration():
     errs = [rel_err(centred(phi), st.phi), rel_err(q2, st.q), rel_err(al2, st.alpha), rel_err(b2, st.beta)]
     print("1024^2 x 2 one iteration: phi, q, alpha, beta", errs)
     assert max(errs) < tol
+
+
+def test_longest_time_axis_one_iteration():
+    """T + 1 = 160 time nodes, the most the mixed path accepts: one iteration from a
+    random state against the oracle, every field (its tcgen05 time passes run a
+    160-long axis: five 32-wide K chunks and a 160-column accumulator)."""
+    D, T, N = 2, 159, [8, 12]
+    rng = np.random.default_rng(159)
+    P = N[0] * N[1]
+    r0, r1 = rng.random(P) + 0.05, rng.random(P) + 0.05
+    g, prob, gpu = pair(D, T, N, r0, r1, prec="mixed", check_every=0)
+    q, al, beta = random_state(g, rng)
+    q = f32(q)
+    sigma = 1.3
+    st = O.State(g, np.zeros(g.n_nodes), np.zeros(g.K * g.n_cones), q.copy(), al.copy(), beta.copy(), sigma)
+    O.iterate(prob, st, tau=1.9)
+    gpu.dot_set_state(q, al, beta, sigma)
+    gpu.dot_solve(tol=0.0, maxit=1)
+    q2, al2, b2, _, it = gpu.dot_get_state()
+    _, _, phi, _, _ = gpu.dot_get()
+    gpu.close()
+    assert it == 1
+    errs = [rel_err(centred(phi), st.phi), rel_err(q2, st.q), rel_err(al2, st.alpha), rel_err(b2, st.beta)]
+    print("T + 1 = 160 one iteration: phi, q, alpha, beta", errs)
+    assert max(errs) < step_tol(T, N)
+
+
+def test_time_axis_beyond_the_limit_is_rejected():
+    """161 time nodes: the mixed path refuses the grid with DOT_EINVAL before any work."""
+    from paper_2505_05424_gb300 import _native as N
+    from paper_2505_05424_gb300.solver import DotError, DotSolver
+    r = np.ones(64)
+    with pytest.raises(DotError) as e:
+        DotSolver(2, 160, [8, 8], r, r, prec="mixed")
+    assert e.value.code == N.DOT_EINVAL

@@ -140,3 +140,41 @@ def test_non_batchable_grid_and_errors():
         srv.release(rid)
         with pytest.raises(DotError):
             srv.result(rid)
+
+
+def test_multilevel_request_matches_context_multilevel():
+    """A request served with the multilevel warm start of Sec. 5 takes the path of
+    dot_solve_multilevel: its coarse level is served as a request of the coarse grid
+    (in that grid's batch) and the prolonged state starts the caller's grid.  Every
+    kernel works on one slot's data, so the result is the context's bit for bit."""
+    N, T, seed = 64, 16, 3701
+    r0, r1, mask = instance(N, T, seed, True)
+    with DotServer(multilevel=1, multilevel_min_nodes=0) as srv:
+        rid = srv.submit(2, T, N, r0, r1, mask=mask, tol=TOL, maxit=MAXIT)
+        assert srv.wait(rid, 600.0) == 0
+        res = srv.result(rid)
+    s = DotSolver(2, T, N, r0, r1, mask=mask, prec="mixed")
+    rc, its = s.dot_solve_multilevel(1, TOL, MAXIT)
+    rho, m, phi, obj, kk = s.dot_get()
+    s.close()
+    assert rc == 0
+    print("multilevel: server", res["kkt"]["iterations"], res["objective"], "context", its, obj)
+    assert res["kkt"]["eta_dot"] <= TOL
+    assert res["kkt"]["iterations"] == kk["iterations"]
+    assert res["objective"] == obj
+    np.testing.assert_array_equal(res["rho"], rho)
+    np.testing.assert_array_equal(res["phi"], phi)
+
+
+def test_multilevel_threshold_and_options():
+    """Requests below multilevel_min_nodes are served cold; bad options are refused."""
+    N, T, seed = 32, 16, 3702
+    st_cold, cold = solve_alone(N, T, seed)
+    with DotServer(multilevel=1, multilevel_min_nodes=10 ** 9) as srv:
+        r0, r1, _ = instance(N, T, seed)
+        rid = srv.submit(2, T, N, r0, r1, tol=TOL, maxit=MAXIT)
+        assert srv.wait(rid, 600.0) == 0
+        res = srv.result(rid)
+    same(cold, res)
+    with pytest.raises(DotError):
+        DotServer(multilevel=9)
