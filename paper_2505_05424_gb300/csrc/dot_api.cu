@@ -501,6 +501,7 @@ int dot_solve(dot_ctx* c, double tol, long maxit) {
       }
     }
     if (checked) {
+      c->path->end_period();
       const double eta = c->kkt[DOT_KKT_ETA];
       if (!std::isfinite(eta)) return fail(c, DOT_EDIVERGED, "stopping measure is not finite");
       if (tol > 0.0 && eta <= tol) return DOT_OK;

@@ -46,6 +46,11 @@ class MixedBatch {
   void set_active(int b, bool on);
   bool active(int b) const { return hp_[b].active != 0; }
   cudaError_t upload_params(cudaStream_t s);
+  // whether the host parameters changed since the last upload
+  bool params_dirty() const { return params_dirty_; }
+  // After a check period: clear every slot's assemble flag (the fused kernels left a
+  // valid residual for each); a penalty change or a new state sets it again.
+  void end_period();
 
   // One iteration of Algorithm 2 for every active slot.
   void iterate(cudaStream_t s, LaunchCounter lc);
@@ -79,6 +84,7 @@ class MixedBatch {
   bool fused_ = false, tma_ = false, fused3_ = false;
   int cur_ = 0;
   bool r_valid_ = false;   // f.r holds the next iteration's residual (from the fused kernel)
+  bool params_dirty_ = true;
   std::unique_ptr<Buffers> B_;
   MxPoisson ps_;
   double* red_ = nullptr;

@@ -13,6 +13,9 @@ struct SlotParam {
                    // iteration after a penalty change (1: nothing to do)
   float tau;       // step length tau of the multiplier updates
   int active;      // 0: the slot holds no solve; its blocks return at once
+  int assemble;    // 1: the first iteration of the next check period assembles this slot's
+                   // lines 1-2 residual (a new or rewritten state, a penalty change); 0: it
+                   // keeps the residual the fused kernel left in f.r
 };
 
 // A batch holds G solves of one grid.  Every per-solve field below is stored as

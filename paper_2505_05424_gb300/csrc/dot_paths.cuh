@@ -105,6 +105,8 @@ class Path {
   virtual int parity() const { return 0; }
   virtual void set_parity(int) {}
   virtual bool residual_carried() const { return false; }
+  // Called once after every check period (host bookkeeping between periods).
+  virtual void end_period() {}
 };
 
 size_t path_workspace_bytes(const Geo& g, dot_precision prec);

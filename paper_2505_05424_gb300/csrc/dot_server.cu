@@ -424,6 +424,7 @@ void dot_server::retire(Batch& b, int k, int status) {
 
 void dot_server::finish_period(Batch& b) {
   b.running = false;
+  b.mb->end_period();
   const int* flag = reinterpret_cast<const int*>(b.h_red + (size_t)b.G * R_NSLOTS);
   if (*flag) {
     for (int k = 0; k < b.G; ++k)

@@ -167,7 +167,8 @@ __device__ __forceinline__ float2 ff_diff(float2 a, float2 b) {
 template <int D>
 __global__ void __launch_bounds__(kThreads, D == 2 ? 4 : 3) k_assemble_residual(Geo g, MxFields fb) {
   const int slot = blockIdx.y;
-  if (!fb.sp[slot].active) return;
+  // a slot without the assemble flag keeps the residual the fused kernel left in f.r
+  if (!fb.sp[slot].active || !fb.sp[slot].assemble) return;
   const float2 isg = fb.sp[slot].isg;
   const MxFields f = slot_view(fb, g, slot);
   const long long n = (long long)(g.T + 1) * g.P;

@@ -124,7 +124,7 @@ cudaError_t down(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 MixedBatch::MixedBatch(const Geo& g, int G, bool slot_masks)
     : g_(g), G_(G), slot_masks_(slot_masks), B_(new Buffers()) {
   std::memset(&ps_, 0, sizeof(ps_));
-  const SlotParam empty{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(1.f, 0.f), 0.f, 0};
+  const SlotParam empty{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(1.f, 0.f), 0.f, 0, 1};
   hp_.assign(G, empty);
   hs_.assign(G, 0.0);
 }
@@ -328,9 +328,12 @@ void MixedBatch::set_sigma(int b, double sigma, double tau, bool rescale) {
     // compose with a factor not yet applied
     const double pending = (double)hp_[b].rescale.x + (double)hp_[b].rescale.y;
     hp_[b].rescale = split_ff(pending * hs_[b] / sigma);
+    hp_[b].assemble = 1;   // c/sigma and the stored multipliers change: the residual too
   } else if (!rescale) {
     hp_[b].rescale = make_float2(1.f, 0.f);
+    hp_[b].assemble = 1;
   }
+  params_dirty_ = true;
   hp_[b].isg = split_ff(1.0 / sigma);
   hp_[b].sg = split_ff(sigma);
   hp_[b].tau = (float)tau;
@@ -352,11 +355,27 @@ void MixedBatch::clear_rescale() {
   for (SlotParam& p : hp_) p.rescale = make_float2(1.f, 0.f);
 }
 
-void MixedBatch::set_active(int b, bool on) { hp_[b].active = on ? 1 : 0; }
+void MixedBatch::set_active(int b, bool on) {
+  hp_[b].active = on ? 1 : 0;
+  params_dirty_ = true;
+}
 
 cudaError_t MixedBatch::upload_params(cudaStream_t s) {
   // pageable source: the runtime stages it before returning, so hp_ may change afterwards
+  params_dirty_ = false;
   return up(dparams_, hp_.data(), (size_t)G_ * sizeof(SlotParam), s);
+}
+
+void MixedBatch::end_period() {
+  // the fused kernels leave every slot's residual in f.r; the last period's first
+  // iteration assembled the flagged slots, so the next one reuses them all unless a
+  // flag is set again (the unfused D = 2 kernel leaves no residual: flags stay set)
+  if (!(tma_ || fused3_)) return;
+  for (SlotParam& p : hp_)
+    if (p.assemble) {
+      p.assemble = 0;
+      params_dirty_ = true;
+    }
 }
 
 void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
@@ -385,7 +404,9 @@ void MixedBatch::iterate(cudaStream_t s, LaunchCounter lc) {
 }
 
 void MixedBatch::kkt(cudaStream_t s, LaunchCounter lc) {
-  r_valid_ = false;   // sigma may change after a check: the next iteration assembles afresh
+  // sigma may change after a check: the next iteration assembles the residual of
+  // every slot whose assemble flag is set (and reuses f.r for the others)
+  r_valid_ = false;
   launch_kkt_mx(g_, G_, cur(), B_->partials, B_->red, fused_ ? B_->socp : nullptr,
                 fused_ ? (int)socp_blocks(g_, G_) : 0, s, lc);
 }
@@ -551,6 +572,7 @@ int MixedBatch::poisson_op(const double* b, double* phi, cudaStream_t s, LaunchC
   std::vector<float2> t(nn);
   if (e == cudaSuccess) e = down(t.data(), B.phi_op, nn * 8, s);
   hp_ = saved;
+  for (SlotParam& p : hp_) p.assemble = 1;   // f.r held the operator's scratch
   if (e == cudaSuccess) e = upload_params(s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { *err = std::string("poisson: ") + cudaGetErrorString(e); return DOT_ECUDA; }
@@ -593,8 +615,11 @@ class PathMixed : public Path {
         batch_.clear_rescale();
         batch_.upload_params(s);
       }
+    } else if (batch_.params_dirty()) {
+      batch_.upload_params(s);   // the assemble flag cleared at the end of the last period
     }
   }
+  void end_period() override { batch_.end_period(); }
   bool graphable() const override { return true; }
   int parity() const override { return batch_.parity(); }
   void set_parity(int p) override { batch_.set_parity(p); }
