@@ -15,7 +15,8 @@
 // beta is read once (plus an L2 re-read in C) and written once; z never reaches
 // HBM.  q, alpha and beta are double-buffered: every read is of iteration k and
 // every write of k+1, so neighbouring CTAs may run at any relative time.
-// The arithmetic per element is the same as k_mixed.cu's unfused kernels.
+// Per element: y and the projection tests in two-float arithmetic, FP32 z and q, two-float
+// face right-hand sides and multiplier updates (ffloat.cuh), as in k_fused3d.cu.
 #include <cmath>
 
 #include "dot_internal.cuh"

@@ -17,9 +17,9 @@
 //             (the warm start of lines 1-2).
 // q, alpha and beta are double-buffered (iteration k read, k+1 written), so the
 // faces on a tile's lower boundary, which both neighbouring tiles compute, are
-// written by one of them only.  The arithmetic of each element is that of the
-// unfused kernels: two-float y, projection, face right-hand sides and multiplier
-// updates (ffloat.cuh), FP32 q and z.
+// written by one of them only.  Per element: two-float y, projection, face
+// right-hand sides and multiplier updates (ffloat.cuh), FP32 q and z, as in the D = 2
+// pass.
 #include <cmath>
 
 #include "dot_internal.cuh"

@@ -369,7 +369,8 @@ cudaError_t MixedBatch::upload_params(cudaStream_t s) {
 void MixedBatch::end_period() {
   // the fused kernels leave every slot's residual in f.r; the last period's first
   // iteration assembled the flagged slots, so the next one reuses them all unless a
-  // flag is set again (the unfused D = 2 kernel leaves no residual: flags stay set)
+  // flag is set again (the D = 2 kernel without TMA, for odd N_y, leaves no residual:
+  // flags stay set)
   if (!(tma_ || fused3_)) return;
   for (SlotParam& p : hp_)
     if (p.assemble) {
