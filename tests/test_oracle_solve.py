@@ -129,3 +129,35 @@ def test_separable_densities_w2():
         errs.append(abs(O.w2_squared(g, res["primal_obj"]) - exact) / exact)
     assert errs[-1] < 0.04
     assert errs[1] < errs[0]
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_feasibility_at_convergence(masked):
+    """At eta_dot <= 1e-7 the iterate is feasible up to the tolerance: the density
+    rho = alpha_0 / h_0 is nonnegative (complementarity part of eta_C), z lies in Q
+    exactly (it is a projection, eq. (app-proj)), B F q + d lies within the primal
+    residual of Q (q in P, eq. (socobservation)), and beta lies in Q = Q^* (the dual
+    cone of the SOCP).  Measured: rho >= -9e-10, z 2e-16, B F q + d 7e-7 and beta
+    1.6e-9 outside their cones."""
+    g = O.Grid(2, 8, [10, 12])
+    rng = np.random.default_rng(91 + masked)
+    P = 120
+    r0, r1 = rng.random(P) + 0.05, rng.random(P) + 0.05
+    r0[rng.random(P) < 0.15] = 0.0          # exact zeros, as in the mixture workloads
+    mask = (rng.random(P) < 0.1) if masked else None
+    prob = O.Problem(g, r0, r1, mask)
+    st = O.State.zeros(g)
+    res = O.solve(prob, st, tol=1e-7, maxit=400000)
+    assert res["eta_dot"] <= 1e-7
+    K = g.K
+
+    def outside(a):   # largest ||a_bar|| - a_0 over the cones (<= 0 inside Q)
+        a = a.reshape(K, -1)
+        return float(np.max(np.linalg.norm(a[1:], axis=0) - a[0]))
+
+    rho = O.density_slices(g, st)
+    assert rho.min() >= -1e-6 * rho.max()
+    assert outside(st.z) <= 1e-13
+    y = O.apply_B(g, prob.omega, O.apply_F(g, st.q)) + O.fill_d(g)
+    assert outside(y) <= 2e-6
+    assert outside(st.beta) <= 1e-7
