@@ -161,3 +161,21 @@ def test_feasibility_at_convergence(masked):
     y = O.apply_B(g, prob.omega, O.apply_F(g, st.q)) + O.fill_d(g)
     assert outside(y) <= 2e-6
     assert outside(st.beta) <= 1e-7
+
+
+def test_identical_densities_static_solution():
+    """rho_0 = rho_1: nothing moves.  The optimum is the static path rho(t) = rho_0,
+    m = 0 with W2^2 = 0 (the Benamou-Brenier cost vanishes only for m = 0).  Measured
+    at eta_dot <= 1e-8: W2^2 = -1.6e-9, rho within 7.7e-6 of rho_0, |m| <= 1.1e-6."""
+    g = O.Grid(2, 8, [12, 10])
+    rng = np.random.default_rng(5)
+    r = rng.random(120) + 0.05
+    prob = O.Problem(g, r, r)
+    st = O.State.zeros(g)
+    res = O.solve(prob, st, tol=1e-8, maxit=400000)
+    assert res["eta_dot"] <= 1e-8
+    assert abs(O.w2_squared(g, res["primal_obj"])) <= 1e-7
+    r0 = (r / r.sum() / O.cell_area(g)).reshape(g.N)
+    rho = O.density_slices(g, st)
+    assert np.abs(rho - r0).max() <= 1e-4 * r0.max()
+    assert max(np.abs(a).max() for a in O.momentum(g, st)) <= 1e-4 * r0.max()
