@@ -94,3 +94,19 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dot_kkt(None, None) == N.DOT_EINVAL
     lib.dot_destroy(None)
     assert lib.dot_launch_count(None) == 0
+
+
+def test_size_limits(lib):
+    """Every field's element index, cone components stacked, stays below 2^31 (the
+    kernels index with 32-bit integers): a grid at the limit is accepted, one beyond
+    it is refused without touching a device."""
+    ok = N.DotGrid(2, 31, (ctypes.c_int * 3)(2048, 2048, 1))      # 32 x 2048^2 x 10 < 2^31
+    assert lib.dot_workspace_bytes(ctypes.byref(ok), N.DOT_MIXED) > 0
+    big = N.DotGrid(2, 63, (ctypes.c_int * 3)(2048, 2048, 1))     # 64 x 2048^2 x 10 >= 2^31
+    assert lib.dot_workspace_bytes(ctypes.byref(big), N.DOT_MIXED) == 0
+    r = np.ones(2048 * 2048)
+    rc, ctx = _create(lib, big, r, r)
+    assert rc == N.DOT_EINVAL and not ctx.value and b"too large" in lib.dot_last_error(None)
+    for D, T, Ns in ((2, 65536, (8, 8, 1)), (2, 4, (65537, 2, 1)), (2, 4, (1, 8, 1))):
+        g = N.DotGrid(D, T, (ctypes.c_int * 3)(*Ns))
+        assert lib.dot_workspace_bytes(ctypes.byref(g), N.DOT_FP64) == 0
