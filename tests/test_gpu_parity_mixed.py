@@ -263,3 +263,25 @@ def test_time_axis_beyond_the_limit_is_rejected():
     with pytest.raises(DotError) as e:
         DotSolver(2, 160, [8, 8], r, r, prec="mixed")
     assert e.value.code == N.DOT_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_identical_densities_move_nothing(prec):
+    """rho_0 = rho_1 (the degenerate problem): both paths solve to eta_dot <= 1e-7 and
+    return the static path rho(t) = rho_0, m = 0, W2^2 = 0 up to the tolerance.  The
+    oracle on this instance at eta_dot <= 1e-7: rho within 6.6e-4 of rho_0 (relative to
+    its maximum), |m| <= 1.9e-5, W2^2 = 4.3e-8 (at 1e-6: 4.8e-3, 1.4e-4, 5.9e-7)."""
+    D, T, N = 2, 16, [32, 32]
+    rng = np.random.default_rng(1601)
+    r = rng.random(1024) + 0.05
+    gpu = pair(D, T, N, r, r, prec=prec)[2]
+    assert gpu.dot_solve(1e-7, 200000) == 0
+    rho, m, phi, obj, kk = gpu.dot_get()
+    gpu.close()
+    r0 = (r / r.sum() * 1024).reshape(N)          # cell-average density of mass 1 on [0, 1]^2
+    dev = np.abs(rho - r0).max() / r0.max()
+    mm = max(np.abs(a).max() for a in m) / r0.max()
+    print(prec, "iterations", kk["iterations"], "W2^2", obj, "rho dev", dev, "m", mm)
+    assert abs(obj) <= 2e-7
+    assert dev <= 2e-3
+    assert mm <= 1e-4
