@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--fp64-maxit", type=int, default=40000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="end-to-end solves through the public API with host buffers, on the timed steps' instances (-1: as many as --steps)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["mix256", "gauss32", "obst128", "mix3d64", "mix1024",
                                                                 "ex1", "ex2", "ex3", "ex4"])
     ap.add_argument("--serve", type=int, default=0,
@@ -372,11 +373,14 @@ def run_ours(args):
                             if algorithmic_bytes(k, spec.D, spec.T, spec.N, args.prec) > 0 and v[1] else None)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0]) if v[1]}
 
-    # e2e through the public API with host buffers: create (H2D) -> solve -> get (D2H)
+    # e2e through the public API with host buffers: create (H2D) -> solve -> get (D2H),
+    # on the same instances as the timed steps (so the two numbers differ by the
+    # end-to-end costs only)
     e2e_lat, e2e_iters = [], []
     h2d = d2h = 0
-    for k in range(args.e2e_steps):
-        r0, r1, m = instance(100 + k)
+    n_e2e = args.steps if args.e2e_steps < 0 else args.e2e_steps
+    for k in range(n_e2e):
+        r0, r1, m = instance(k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = make_solver(spec, r0, r1, m, args.prec, check_every=args.check_every)
@@ -408,7 +412,7 @@ def run_ours(args):
         "clocks": clk, "gpu_launches": int(gpu_launches),
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "iterations": e2e_iters,
-                "seeds": f"{base_seed}+100+step" if base_seed is not None else None},
+                "seeds": f"{base_seed}+step (the timed steps' instances)" if base_seed is not None else None},
         "roofline": roof, "kernels": kernels,
     }
 
