@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="arrivals per second of the serving stream")
     ap.add_argument("--serve-multilevel", type=int, default=0,
                     help="serve large requests with the multilevel warm start over this many coarse levels")
+    ap.add_argument("--serve-ml-masked", action="store_true",
+                    help="also warm-start requests with obstacles")
     ap.add_argument("--serve-ml-min-nodes", type=int, default=500000,
                     help="requests with at least this many nodes get the multilevel warm start")
     ap.add_argument("--serve-maxit", type=int, default=300000,
@@ -534,7 +536,8 @@ def run_serve(args):
         for i in ids:
             srv.wait(i)
     clocks = ClockSampler(0)
-    srv = DotServer(multilevel=args.serve_multilevel, multilevel_min_nodes=args.serve_ml_min_nodes)
+    srv = DotServer(multilevel=args.serve_multilevel, multilevel_min_nodes=args.serve_ml_min_nodes,
+                    multilevel_masked=args.serve_ml_masked)
     clocks.start()
     t0 = time.perf_counter()
     ids = []
@@ -572,6 +575,7 @@ def run_serve(args):
                                   "obstacles, seeded mixtures (seed 50000+i)", "tol": args.tol,
                       "maxit": args.serve_maxit, "multilevel": args.serve_multilevel,
                       "multilevel_min_nodes": args.serve_ml_min_nodes,
+                      "multilevel_masked": bool(args.serve_ml_masked),
                       "arrivals_span_s": round(reqs[-1][0], 3) if reqs else 0.0},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "queue_p50": float(np.percentile(qwait, 50)), "queue_p99": float(np.percentile(qwait, 99))},

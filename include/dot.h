@@ -266,6 +266,9 @@ typedef struct {
   long long multilevel_min_nodes;  /* only requests with at least this many nodes (T+1) N_1..N_D and a
                                       grid divisible by 2^multilevel (default 1,000,000) */
   double multilevel_coarse_tol;    /* tolerance of the coarse levels; 0 = max(tol 10^-v, 1e-6) */
+  int multilevel_masked;           /* 1: warm-start requests with obstacles too; 0 (default): serve them
+                                      cold (their coarse levels, with obstacles grown to whole blocks,
+                                      measured slower than a cold start) */
 } dot_server_options;
 
 void dot_server_default_options(dot_server_options *o);

@@ -86,7 +86,8 @@ class DotOptions(ctypes.Structure):
 class DotServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("target_nodes", ctypes.c_long),
                 ("use_graphs", ctypes.c_int), ("idle_ms", ctypes.c_int), ("multilevel", ctypes.c_int),
-                ("multilevel_min_nodes", ctypes.c_longlong), ("multilevel_coarse_tol", ctypes.c_double)]
+                ("multilevel_min_nodes", ctypes.c_longlong), ("multilevel_coarse_tol", ctypes.c_double),
+                ("multilevel_masked", ctypes.c_int)]
 
 
 DOT_OK, DOT_EINVAL, DOT_ENOMEM, DOT_ECUDA, DOT_EDIVERGED, DOT_ETIMEOUT, DOT_ENOTCONV = 0, -1, -2, -3, -4, -5, 1

@@ -545,6 +545,7 @@ void dot_server_default_options(dot_server_options* o) {
   o->multilevel = 0;
   o->multilevel_min_nodes = 1000000;
   o->multilevel_coarse_tol = 0.0;
+  o->multilevel_masked = 0;
 }
 
 int dot_server_create(const dot_options* opt, const dot_server_options* sopt, dot_server** out) {
@@ -606,7 +607,8 @@ int dot_server_submit(dot_server* s, const dot_grid* grid, const double* rho0, c
   r->keep = keep_fields != 0;
   const int L = s->sopt.multilevel;
   std::string mwhy;
-  if (L > 0 && nodes_of(*grid) >= s->sopt.multilevel_min_nodes && multilevel_ok(*grid, L, &mwhy)) {
+  if (L > 0 && nodes_of(*grid) >= s->sopt.multilevel_min_nodes && (!r->has_mask || s->sopt.multilevel_masked) &&
+      multilevel_ok(*grid, L, &mwhy)) {
     // the pyramid of the multilevel strategy, served coarsest first: the prepared
     // densities and the obstacle cells (weight != 1) averaged as dot_solve_multilevel
     // averages a context's

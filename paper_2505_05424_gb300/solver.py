@@ -239,7 +239,8 @@ class DotServer:
 
     def __init__(self, hbm_budget: int = 0, max_slots: int = 64, target_nodes: int = 4194304,
                  use_graphs: bool = True, idle_ms: int = 200, multilevel: int = 0,
-                 multilevel_min_nodes: int = 1000000, multilevel_coarse_tol: float = 0.0, **options):
+                 multilevel_min_nodes: int = 1000000, multilevel_coarse_tol: float = 0.0,
+                 multilevel_masked: bool = False, **options):
         import torch  # the device only
         if not torch.cuda.is_available():
             raise RuntimeError("DotServer needs a CUDA device (no CPU fallback)")
@@ -256,6 +257,7 @@ class DotServer:
         so.multilevel = int(multilevel)
         so.multilevel_min_nodes = int(multilevel_min_nodes)
         so.multilevel_coarse_tol = float(multilevel_coarse_tol)
+        so.multilevel_masked = int(bool(multilevel_masked))
         srv = ctypes.c_void_p()
         rc = self.lib.dot_server_create(ctypes.byref(self.opt), ctypes.byref(so), ctypes.byref(srv))
         if rc != N.DOT_OK:

@@ -149,7 +149,7 @@ def test_multilevel_request_matches_context_multilevel():
     kernel works on one slot's data, so the result is the context's bit for bit."""
     N, T, seed = 64, 16, 3701
     r0, r1, mask = instance(N, T, seed, True)
-    with DotServer(multilevel=1, multilevel_min_nodes=0) as srv:
+    with DotServer(multilevel=1, multilevel_min_nodes=0, multilevel_masked=True) as srv:
         rid = srv.submit(2, T, N, r0, r1, mask=mask, tol=TOL, maxit=MAXIT)
         assert srv.wait(rid, 600.0) == 0
         res = srv.result(rid)
@@ -167,7 +167,8 @@ def test_multilevel_request_matches_context_multilevel():
 
 
 def test_multilevel_threshold_and_options():
-    """Requests below multilevel_min_nodes are served cold; bad options are refused."""
+    """Requests below multilevel_min_nodes, and masked requests unless
+    multilevel_masked, are served cold; bad options are refused."""
     N, T, seed = 32, 16, 3702
     st_cold, cold = solve_alone(N, T, seed)
     with DotServer(multilevel=1, multilevel_min_nodes=10 ** 9) as srv:
@@ -176,5 +177,12 @@ def test_multilevel_threshold_and_options():
         assert srv.wait(rid, 600.0) == 0
         res = srv.result(rid)
     same(cold, res)
+    st_m, cold_m = solve_alone(N, T, seed + 1, True)
+    with DotServer(multilevel=1, multilevel_min_nodes=0) as srv:
+        r0, r1, mask = instance(N, T, seed + 1, True)
+        rid = srv.submit(2, T, N, r0, r1, mask=mask, tol=TOL, maxit=MAXIT)
+        assert srv.wait(rid, 600.0) == 0
+        res = srv.result(rid)
+    same(cold_m, res)
     with pytest.raises(DotError):
         DotServer(multilevel=9)
