@@ -65,7 +65,6 @@ struct Request {
   double tol_final = 1e-6;
   std::vector<double> init_q, init_al, init_beta;   // prolonged state for the next admission
   double init_sigma = 0.0;
-  long coarse_iters = 0;
 };
 
 struct Batch {
@@ -372,7 +371,6 @@ bool dot_server::next_level(Batch& b, int k) {
                         r->init_beta.data()) != DOT_OK)
     return false;
   r->init_sigma = r->sigma;
-  r->coarse_iters += r->iters;
   if (set_level(r, r->lv + 1, opt, sopt.multilevel_coarse_tol, &why) != DOT_OK) return false;
   b.mb->set_active(k, false);
   b.slot[k] = nullptr;
