@@ -232,7 +232,10 @@ class DotServer:
 
     submit() returns a request id; wait() blocks until it finished; result()
     returns (objective, kkt dict, times (submit, admit, done) in seconds since the
-    server started, and rho/m/phi when the request kept its fields)."""
+    server started, and rho/m/phi when the request kept its fields).  The keyword
+    arguments are the fields of dot_server_options (multilevel > 0: the multilevel
+    warm start for requests of at least multilevel_min_nodes nodes, obstacle
+    requests only with multilevel_masked); **options are those of dot_options."""
 
     STATS = ("queued", "running", "finished", "batches", "bytes", "graph_launches", "kernel_launches",
              "peak_running", "peak_batches")
